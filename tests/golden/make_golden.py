@@ -1,0 +1,57 @@
+"""Writes the stored expected values under tests/golden/ from the oracle alone.
+
+Run from the repository root:  python tests/golden/make_golden.py
+Every value here comes from ``oracle/`` (Algorithm 1 with dense eigensolves,
+or a closed form); nothing comes from the CUDA path.
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import instances as I  # noqa: E402
+from oracle import closed_forms as CF  # noqa: E402
+from oracle import rmc_oracle as O  # noqa: E402
+
+
+def dump(name, payload):
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(payload, f, indent=1)
+        f.write("\n")
+
+
+def main():
+    c1 = I.tfim_n8()
+    r1 = O.solve(c1)
+    c1f = I.tfim_n8(); c1f.k = 16
+    dump("tfim_n8.json", {
+        "source": "oracle (Algorithm 1, dense eigh) and exact diagonalisation of the 256-dim chain",
+        "chain": c1.to_json(),
+        "energies_k8": r1.energies.tolist(),
+        "energies_k16": O.solve(c1f).energies.tolist(),
+        "exact": O.exact_spectrum(c1, 4).tolist(),
+        "merges": [[m.lo, m.mid, m.hi, m.k_ret, m.k_eff] for m in r1.merges],
+    })
+    c2 = I.xxz_n32()
+    r2 = O.solve(c2)
+    dump("xxz_n32_k64.json", {
+        "source": "oracle (Algorithm 1, dense eigh), XXZ N=32, Delta=1, J_i~U[0.5,1.5] seed 260902",
+        "chain": c2.to_json(),
+        "energies": r2.energies.tolist(),
+        "merges": [[m.lo, m.mid, m.hi, m.k_ret, m.k_eff] for m in r2.merges],
+        "theta_low": [m.theta[: m.k_ret + 8].tolist() for m in r2.merges],
+    })
+    ff = {}
+    for N in (16, 24, 32, 48, 64, 128):
+        for h in (0.2, 0.7, 1.0, 2.0):
+            ff[f"{N}_{h}"] = CF.tfim_lowest(N, 1.0, h, 16).tolist()
+    dump("tfim_free_fermion.json", {
+        "source": "free-fermion closed form (singular values of the bidiagonal h/J matrix)",
+        "lowest16": ff,
+    })
+
+
+if __name__ == "__main__":
+    main()
