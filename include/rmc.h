@@ -1,0 +1,243 @@
+/*
+ * rmc.h -- C ABI of the recursive module-coupling eigensolver (B300, sm_103a).
+ *
+ * The library computes Algorithm 1 of "A Recursive Module-Coupling Algorithm
+ * for Computing Low-Energy Eigenstates" (arXiv 2609.02394) on one GPU:
+ * diagonalise small leaf modules (Sec. II, Eq. (4)); repeatedly couple two
+ * neighbouring blocks A and B, solving for the lowest eigenpairs of the
+ * effective Hamiltonian in the product basis of their retained states,
+ *     H_eff = diag(E_A[a] + E_B[b]) + sum_j coef_j o_A^j (x) o_B^j      (Eq. (7))
+ * (the minus sign of Eq. (3) is folded into coef_j), keeping the lowest states
+ * (Eq. (10)) and rotating the boundary operators the next merge needs into the
+ * new basis (Algorithm 1, inner loop); return the lowest q eigenpairs of the
+ * final block.  The effective Hamiltonian is never formed: every product with
+ * it is a Kronecker-form product Y = D o X + sum_j coef_j O_A^j X (O_B^j)^T on
+ * the k_A x k_B coefficient matrix X of a product-basis vector.
+ *
+ * Conventions
+ *   - Product-basis index: row = a * k_B + b (a from module A is the slow
+ *     index, Eq. (5)); a vector is a row-major k_A x k_B matrix.
+ *   - All host arrays are row-major, FP64, owned by the caller and copied at
+ *     call time.  All blocks are opaque device-resident handles owned by the
+ *     caller and released with rmc_block_free.  No call consumes its inputs.
+ *   - Calls are ordered on the context's CUDA stream.  rmc_couple and
+ *     rmc_solve_chain synchronise with the host between solver iterations
+ *     (convergence is checked on the host); rmc_lowest and the export calls
+ *     synchronise before returning.  One context per host thread.
+ *   - Every call returns an rmc_status; on failure rmc_last_error(ctx) returns
+ *     a one-line description.  A failed call leaves its outputs unset and
+ *     frees whatever it allocated.
+ *
+ * Kernel-level entry points (rmc_kron_matvec, ...) take DEVICE pointers and
+ * run one kernel of the hot path on the given stream; they exist so that each
+ * step can be checked on its own against the CPU oracle.
+ */
+#ifndef RMC_H_
+#define RMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rmc_status {
+  RMC_OK = 0,
+  RMC_ERR_INVAL = 1,    /* bad argument: sizes, NaN, asymmetric H, unknown op */
+  RMC_ERR_NOMEM = 2,    /* request exceeds the context's device-memory budget */
+  RMC_ERR_NOCONV = 3,   /* eigensolver hit max_iter; best Ritz values kept   */
+  RMC_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up                 */
+  RMC_ERR_CUDA = 5      /* a CUDA runtime call failed                         */
+} rmc_status;
+
+typedef enum rmc_precision {
+  /* Every floating-point step in FP64 (DFMA): the plain per-solve form. */
+  RMC_PREC_FP64 = 0,
+  /* Filter, orthogonalisation and Rayleigh-Ritz of the subspace iteration in
+   * FP32 (FP32 accumulation); every merge then ends with the FP64
+   * finalisation (FP64 Cholesky-QR, FP64 Rayleigh-Ritz with refined
+   * eigenvectors, FP64 rotation), so energies and retained bases are FP64-
+   * consistent projections. */
+  RMC_PREC_MIXED = 1,
+  /* As RMC_PREC_MIXED with the Kronecker products of the filter on the tcgen05
+   * tensor cores (TF32 operands, FP32 accumulation). */
+  RMC_PREC_MIXED_TF32 = 2
+} rmc_precision;
+
+typedef struct rmc_config {
+  int device;              /* CUDA device ordinal                               */
+  void* stream;            /* cudaStream_t to run on; NULL: the library makes one */
+  size_t mem_budget;       /* bytes of device memory the context may hold; 0: 40 GiB */
+  int precision;           /* rmc_precision                                    */
+  double tol;              /* residual tolerance (relative to max(1,|theta|)) of
+                              the working-precision solve; <= 0: 1e-11 (FP64),
+                              2e-6 (mixed)                                      */
+  int max_iter;            /* outer subspace iterations per merge; <= 0: 200   */
+  int guard;               /* extra vectors beyond the retained count; <= 0:
+                              max(16, k_ret / 2), capped by the dimension       */
+  double tau_deg;          /* degenerate-cut threshold; <= 0: 1e-7              */
+} rmc_config;
+
+typedef struct rmc_ctx rmc_ctx;
+typedef struct rmc_block rmc_block;
+
+/* Tags of the operators a block carries, so that callers can look them up:
+ * site index (chain-global) and a Pauli letter ('X', 'Y', 'Z'; 'Y' is carried
+ * as the real matrix iY = [[0,1],[-1,0]]) or 'O' for an arbitrary operator. */
+typedef struct rmc_op_tag {
+  int site;
+  char pauli;
+} rmc_op_tag;
+
+/* One coupling term of a merge: coef * o_A[op_a] (x) o_B[op_b]  (Eq. (3)/(8)). */
+typedef struct rmc_term {
+  double coef;
+  int op_a;
+  int op_b;
+} rmc_term;
+
+/* An operator to carry into the merged block: side 0 = from A (rotated as
+ * C^T (o (x) I) C), side 1 = from B (rotated as C^T (I (x) o) C). */
+typedef struct rmc_carry {
+  int side;
+  int op;
+} rmc_carry;
+
+/* Flags of rmc_couple. */
+#define RMC_COUPLE_TOP 1   /* top level: keep exactly k_keep, skip the degenerate cut */
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on cfg->device (cfg may be NULL for all defaults). */
+rmc_status rmc_create(rmc_ctx** ctx, const rmc_config* cfg);
+/* Destroy a context; blocks still alive are freed with it. */
+rmc_status rmc_destroy(rmc_ctx* ctx);
+/* Text of the last error on this context ("" if none).  Owned by ctx. */
+const char* rmc_last_error(const rmc_ctx* ctx);
+/* Bytes of device memory currently held (blocks + cached workspace). */
+size_t rmc_mem_in_use(const rmc_ctx* ctx);
+/* Counters since creation: kernel launches issued, outer iterations run. */
+rmc_status rmc_stats(const rmc_ctx* ctx, uint64_t* launches, uint64_t* iterations);
+/* The stream the context runs on (a cudaStream_t). */
+void* rmc_stream(const rmc_ctx* ctx);
+
+/* ---- Algorithm 1 --------------------------------------------------------- */
+
+/* Leaf module (Algorithm 1, first step; Eqs. (4), (9)).
+ *   H    : D x D row-major module Hamiltonian; must be symmetric within 1e-12
+ *          (relative to max|H|) and finite, else RMC_ERR_INVAL.
+ *   k    : number of lowest states to keep; the kept count is min(k, D),
+ *          reduced by the degenerate-cut rule so no multiplet is split.
+ *   ops  : n_ops pointers to D x D operators to carry (projected o = U^T O U).
+ *   tags : n_ops tags (may be NULL).
+ * On success *out is a new block with energies (ascending), carried
+ * operators and the D x k eigenvector matrix U. 1 <= D <= 256. */
+rmc_status rmc_build_leaf(rmc_ctx* ctx, const double* H, int D, int k,
+                          const double* const* ops, const rmc_op_tag* tags,
+                          int n_ops, rmc_block** out);
+
+/* Pauli-term leaf: the module Hamiltonian of L sites (D = 2^L <= 256) is built
+ * on the device from on-site terms coef*P_site and bond terms coef*P_i P_j
+ * (site indices local, 0 = most significant factor; Y Y is written as
+ * -(iY)(iY)); carried operators are the single-site Paulis in `carry`.
+ * onsite: n_onsite triples (site, pauli, coef) packed as
+ *         int sites[n], char paulis[n], double coefs[n]; bonds likewise. */
+rmc_status rmc_build_leaf_pauli(rmc_ctx* ctx, int L, int k,
+                                int n_onsite, const int* onsite_site,
+                                const char* onsite_pauli, const double* onsite_coef,
+                                int n_bonds, const int* bond_i, const int* bond_j,
+                                const char* bond_pauli_i, const char* bond_pauli_j,
+                                const double* bond_coef,
+                                int n_carry, const rmc_op_tag* carry, rmc_block** out);
+
+/* One merge of Algorithm 1 (inner loop; Eqs. (5)-(10)).
+ *   terms  : the coupling V = sum coef o_A[op_a] (x) o_B[op_b]; A and B may be
+ *            the same block (homogeneous reuse: identical modules).
+ *   k_keep : states to keep: min(k_keep, k_A k_B), then the degenerate-cut rule
+ *            (largest k' with theta[k'] - theta[k'-1] > tau max(1,|theta[k']|))
+ *            unless flags has RMC_COUPLE_TOP.
+ *   carry  : which of A's and B's operators to rotate into the new block
+ *            (Algorithm 1: "transform the projected boundary operators
+ *            required at the next merge"); tags are inherited.
+ * The lowest eigenpairs are found by Chebyshev-filtered subspace iteration on
+ * the Kronecker-form product, then finalised in FP64.  RMC_ERR_NOCONV when
+ * max_iter is reached (*out is still produced from the best iterate). */
+rmc_status rmc_couple(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B,
+                      const rmc_term* terms, int n_terms, int k_keep,
+                      const rmc_carry* carry, int n_carry, int flags,
+                      rmc_block** out);
+
+/* Lowest q energies of a block (Algorithm 1, last step), ascending, into the
+ * host array E_out[q]; q is clipped to the block's kept count, which is
+ * written to *k_eff_out (may be NULL).  C_out (may be NULL) receives the
+ * block's coefficient matrix, row-major (k_A k_B) x q (or D x q for a leaf). */
+rmc_status rmc_lowest(rmc_ctx* ctx, const rmc_block* blk, int q, double* E_out,
+                      double* C_out, int* k_eff_out);
+
+/* Whole chain (the recursion loop of Algorithm 1): sites 0..n_sites-1 with
+ * on-site terms and two-site terms (i < j) as in rmc_build_leaf_pauli but with
+ * chain-global site indices; the chain is split into floor/ceil halves until a
+ * part has <= L0 sites; every level keeps k states, the top returns q.
+ * E_out[q] receives the lowest energies (host). */
+rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, int q,
+                           int n_onsite, const int* onsite_site,
+                           const char* onsite_pauli, const double* onsite_coef,
+                           int n_bonds, const int* bond_i, const int* bond_j,
+                           const char* bond_pauli_i, const char* bond_pauli_j,
+                           const double* bond_coef, double* E_out);
+
+/* ---- blocks -------------------------------------------------------------- */
+
+rmc_status rmc_block_free(rmc_ctx* ctx, rmc_block* blk);
+/* Kept count k, number of carried operators, basis rows (D for a leaf,
+ * k_A k_B for a merged block), and the tag of each operator (tags may be NULL,
+ * else n_ops entries). */
+rmc_status rmc_block_info(const rmc_block* blk, int* k, int* n_ops, int* basis_rows,
+                          rmc_op_tag* tags);
+/* Copy a block to host arrays: E[k], ops (n_ops x k x k), basis (rows x k,
+ * row-major).  Any pointer may be NULL to skip that part. Synchronises. */
+rmc_status rmc_block_export(rmc_ctx* ctx, const rmc_block* blk, double* E,
+                            double* ops, double* basis);
+/* A block from host data (energies ascending, operators k x k each); the
+ * basis is optional (rows = 0 to omit).  Used for checkpoints and for
+ * per-merge checks against the oracle. */
+rmc_status rmc_block_import(rmc_ctx* ctx, int k, const double* E, int n_ops,
+                            const double* ops, const rmc_op_tag* tags, int rows,
+                            const double* basis, rmc_block** out);
+
+/* ---- kernel-level entry points (device pointers, one step each) ----------- */
+
+/* The Kronecker-form product with the effective Hamiltonian of Eq. (7) for a
+ * block of nv vectors:
+ *   Y[v] = alpha * (D o X[v] + sum_j coef_j A_j X[v] B_j^T) + beta * X[v] + gamma * Z[v]
+ * with D[a][b] = EA[a] + EB[b].  X, Y, Z: nv x kA x kB (Z may be NULL when
+ * gamma == 0; Y must not alias X or Z); A: n_ops x kA x kA; B: n_ops x kB x kB;
+ * EA[kA], EB[kB], coef[n_ops]: all device pointers of `dtype` (0 = FP64,
+ * 1 = FP32; coef, alpha, beta, gamma are always double on the host side and
+ * coef is a host array).  The intermediate products are held in scratch
+ * memory the library allocates from the context (RMC_ERR_NOMEM if the budget
+ * is exceeded).  Runs on the context stream; does not synchronise. */
+rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv,
+                           const void* EA, const void* EB, const void* A, const void* B,
+                           const double* coef, const void* X, void* Y, const void* Z,
+                           double alpha, double beta, double gamma);
+
+/* Lowest eigenpairs of a symmetric m x m FP64 matrix (device pointers): all m
+ * eigenvalues ascending into w[m], eigenvectors as columns of the row-major
+ * m x m matrix V.  FP32 parallel Jacobi followed by FP64 refinement of the
+ * eigenvector matrix (Ogita-Aishima).  1 <= m <= 160. */
+rmc_status rmc_syev(rmc_ctx* ctx, int m, const double* S, double* w, double* V);
+
+/* Rotation of one carried operator into the merged basis (Algorithm 1:
+ * "transform the projected boundary operators"): out = C^T (o (x) I_kB) C
+ * (side 0) or C^T (I_kA (x) o) C (side 1).  C: kr vectors of kA x kB (device,
+ * FP64, vector-major), o: k x k (k = kA or kB), out: kr x kr. */
+rmc_status rmc_rotate_op(rmc_ctx* ctx, int side, int kA, int kB, int kr,
+                         const double* C, const double* o, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMC_H_ */

@@ -13,13 +13,16 @@ from .rmc_oracle import (  # noqa: F401
     boundary_ops,
     carried_matrix,
     cut_rule,
+    effective_hamiltonian,
     exact_spectrum,
     full_chain_hamiltonian,
     gauge_fix,
     leaf_block,
     merge_blocks,
     merge_terms,
+    lift_states,
     pauli_matrix,
+    rotate_operator,
     solve,
     split_tree,
 )

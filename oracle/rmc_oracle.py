@@ -222,15 +222,31 @@ def leaf_block(chain: Chain, lo: int, hi: int, k: int, is_top: bool = False) -> 
     return Block(lo, hi, w[:k_eff].copy(), ops, U, True)
 
 
+def effective_hamiltonian(EA: np.ndarray, EB: np.ndarray, coupling) -> np.ndarray:
+    """Eq. (7) written out: diag(E_A[a] + E_B[b]) + sum coef * kron(o_A, o_B),
+    with ``coupling`` a list of (coef, o_A, o_B) in the retained bases."""
+    kA, kB = len(EA), len(EB)
+    H = np.kron(np.diag(EA), np.eye(kB)) + np.kron(np.eye(kA), np.diag(EB))
+    for coef, oA, oB in coupling:
+        H += coef * np.kron(oA, oB)
+    return H
+
+
+def rotate_operator(C: np.ndarray, o: np.ndarray, side: int, kA: int, kB: int) -> np.ndarray:
+    """Algorithm 1's operator transform: C^T kron(o, I) C for an operator of
+    module A (side 0), C^T kron(I, o) C for one of module B (side 1)."""
+    big = np.kron(o, np.eye(kB)) if side == 0 else np.kron(np.eye(kA), o)
+    return C.T @ big @ C
+
+
 def merge_blocks(chain: Chain, A: Block, B: Block, k: int, is_top: bool,
                  keep_matrix: bool = False) -> Tuple[Block, MergeRecord]:
     """One merge of Algorithm 1: product basis, projected couplings, dense
     H_eff (Eq. (7)), full eigendecomposition (Eq. (10)), keep, rotate."""
     kA, kB = len(A.E), len(B.E)
     n = kA * kB
-    H = np.kron(np.diag(A.E), np.eye(kB)) + np.kron(np.eye(kA), np.diag(B.E))
-    for coef, ka, kb in merge_terms(chain, A.lo, A.hi, B.lo, B.hi):
-        H += coef * np.kron(A.ops[ka], B.ops[kb])
+    H = effective_hamiltonian(A.E, B.E, [(coef, A.ops[ka], B.ops[kb])
+                                         for coef, ka, kb in merge_terms(chain, A.lo, A.hi, B.lo, B.hi)])
     if not np.allclose(H, H.T, atol=1e-12, rtol=0):
         raise AssertionError("effective Hamiltonian is not symmetric")
     theta, V = np.linalg.eigh(H)
@@ -246,10 +262,9 @@ def merge_blocks(chain: Chain, A: Block, B: Block, k: int, is_top: bool,
         for key in boundary_ops(chain, A.lo, B.hi):
             site, _ = key
             if A.lo <= site < A.hi:
-                big = np.kron(A.ops[key], np.eye(kB))
+                ops[key] = rotate_operator(C, A.ops[key], 0, kA, kB)
             else:
-                big = np.kron(np.eye(kA), B.ops[key])
-            ops[key] = C.T @ big @ C
+                ops[key] = rotate_operator(C, B.ops[key], 1, kA, kB)
     blk = Block(A.lo, B.hi, theta[:k_eff].copy(), ops, C, False, (A, B))
     rec = MergeRecord(A.lo, A.hi, B.hi, H if keep_matrix else None, theta, k_ret, k_eff)
     return blk, rec

@@ -1,0 +1,277 @@
+"""B300-native recursive module-coupling eigensolver (arXiv 2609.02394).
+
+Thin ctypes binding over the C ABI in ``include/rmc.h`` (``librmc.so``):
+argument marshalling only -- every step of Algorithm 1 runs in the library's
+CUDA kernels.  There is no CPU fallback: if the library is missing or no CUDA
+device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librmc.so")
+
+RMC_OK, RMC_ERR_INVAL, RMC_ERR_NOMEM, RMC_ERR_NOCONV, RMC_ERR_TIMEOUT, RMC_ERR_CUDA = range(6)
+STATUS_NAMES = {0: "RMC_OK", 1: "RMC_ERR_INVAL", 2: "RMC_ERR_NOMEM", 3: "RMC_ERR_NOCONV",
+                4: "RMC_ERR_TIMEOUT", 5: "RMC_ERR_CUDA"}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_tf32": 2}
+RMC_COUPLE_TOP = 1
+
+EXPORTED = [
+    "rmc_create", "rmc_destroy", "rmc_last_error", "rmc_mem_in_use", "rmc_stats", "rmc_stream",
+    "rmc_build_leaf", "rmc_build_leaf_pauli", "rmc_couple", "rmc_lowest", "rmc_solve_chain",
+    "rmc_block_free", "rmc_block_info", "rmc_block_export", "rmc_block_import",
+    "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op",
+]
+
+
+class RmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rmc_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
+                ("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("guard", ctypes.c_int), ("tau_deg", ctypes.c_double)]
+
+
+class rmc_op_tag(ctypes.Structure):
+    _fields_ = [("site", ctypes.c_int), ("pauli", ctypes.c_char)]
+
+
+class rmc_term(ctypes.Structure):
+    _fields_ = [("coef", ctypes.c_double), ("op_a", ctypes.c_int), ("op_b", ctypes.c_int)]
+
+
+class rmc_carry(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int), ("op", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2609_02394_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp, cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_char_p
+    P = ctypes.POINTER
+    sig = {
+        "rmc_create": ([P(vp), P(rmc_config)], ip),
+        "rmc_destroy": ([vp], ip),
+        "rmc_last_error": ([vp], cp),
+        "rmc_mem_in_use": ([vp], ctypes.c_size_t),
+        "rmc_stats": ([vp, P(ctypes.c_uint64), P(ctypes.c_uint64)], ip),
+        "rmc_stream": ([vp], vp),
+        "rmc_build_leaf": ([vp, P(dp), ip, ip, P(P(dp)), P(rmc_op_tag), ip, P(vp)], ip),
+        "rmc_build_leaf_pauli": ([vp, ip, ip, ip, P(ip), cp, P(dp), ip, P(ip), P(ip), cp, cp, P(dp), ip,
+                                  P(rmc_op_tag), P(vp)], ip),
+        "rmc_couple": ([vp, vp, vp, P(rmc_term), ip, ip, P(rmc_carry), ip, ip, P(vp)], ip),
+        "rmc_lowest": ([vp, vp, ip, P(dp), P(dp), P(ip)], ip),
+        "rmc_solve_chain": ([vp, ip, ip, ip, ip, ip, P(ip), cp, P(dp), ip, P(ip), P(ip), cp, cp, P(dp), P(dp)], ip),
+        "rmc_block_free": ([vp, vp], ip),
+        "rmc_block_info": ([vp, P(ip), P(ip), P(ip), P(rmc_op_tag)], ip),
+        "rmc_block_export": ([vp, vp, P(dp), P(dp), P(dp)], ip),
+        "rmc_block_import": ([vp, ip, P(dp), ip, P(dp), P(rmc_op_tag), ip, P(dp), P(vp)], ip),
+        "rmc_kron_matvec": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
+        "rmc_syev": ([vp, ip, vp, vp, vp], ip),
+        "rmc_rotate_op": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Block:
+    """Opaque device-resident block handle (freed with its context or .free())."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p(handle)
+
+    def info(self):
+        k, n_ops, rows = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.ctx.lib.rmc_block_info(self.handle, ctypes.byref(k), ctypes.byref(n_ops), ctypes.byref(rows), None)
+        tags = (rmc_op_tag * max(1, n_ops.value))()
+        self.ctx.lib.rmc_block_info(self.handle, None, None, None, tags)
+        return k.value, n_ops.value, rows.value, [(tags[j].site, tags[j].pauli.decode()) for j in range(n_ops.value)]
+
+    def export(self):
+        """(E[k], ops[n_ops, k, k], basis[k, rows]) as FP64 numpy arrays."""
+        k, n_ops, rows, _ = self.info()
+        E = np.empty(k)
+        ops = np.empty((max(n_ops, 1), k, k))
+        basis = np.empty((k, max(rows, 1)))
+        self.ctx._check(self.ctx.lib.rmc_block_export(self.ctx.h, self.handle, _dptr(E), _dptr(ops),
+                                                      _dptr(basis) if rows else None))
+        return E, ops[:n_ops], (basis if rows else None)
+
+    def free(self):
+        if self.handle:
+            self.ctx._check(self.ctx.lib.rmc_block_free(self.ctx.h, self.handle))
+            self.handle = ctypes.c_void_p(0)
+
+
+class Context:
+    """One solver context (device, stream, memory budget, precision)."""
+
+    def __init__(self, device: int = 0, precision: str = "fp64", stream: Optional[int] = None,
+                 mem_budget: int = 0, tol: float = 0.0, max_iter: int = 0, guard: int = 0, tau_deg: float = 0.0):
+        self.lib = load_library()
+        cfg = rmc_config(device, ctypes.c_void_p(stream) if stream else None, mem_budget, PRECISIONS[precision],
+                         tol, max_iter, guard, tau_deg)
+        h = ctypes.c_void_p()
+        st = self.lib.rmc_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != RMC_OK:
+            raise RmcError(st, "rmc_create failed")
+        self.h = h
+        self.precision = precision
+
+    def close(self):
+        if self.h:
+            self.lib.rmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st: int, allow=()):
+        if st != RMC_OK and st not in allow:
+            raise RmcError(st, self.lib.rmc_last_error(self.h).decode())
+        return st
+
+    def last_error(self) -> str:
+        return self.lib.rmc_last_error(self.h).decode()
+
+    @property
+    def stream(self) -> int:
+        return self.lib.rmc_stream(self.h)
+
+    def stats(self):
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self.lib.rmc_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def mem_in_use(self) -> int:
+        return self.lib.rmc_mem_in_use(self.h)
+
+    # ---- Algorithm 1 -------------------------------------------------------
+    def build_leaf(self, H, k: int, ops: Sequence = (), tags: Sequence = ()) -> Block:
+        H = _f64(H)
+        D = H.shape[0]
+        opsl = [_f64(o) for o in ops]
+        arr = (ctypes.POINTER(ctypes.c_double) * max(1, len(opsl)))(*[_dptr(o) for o in opsl])
+        tg = (rmc_op_tag * max(1, len(opsl)))(*[rmc_op_tag(s, p.encode()) for s, p in tags]) if tags else None
+        out = ctypes.c_void_p()
+        self._check(self.lib.rmc_build_leaf(self.h, _dptr(H), D, k, arr, tg, len(opsl), ctypes.byref(out)))
+        return Block(self, out.value)
+
+    def build_leaf_pauli(self, L: int, k: int, onsite, bonds, carry) -> Block:
+        os_ = np.array([t[0] for t in onsite], dtype=np.int32)
+        op_ = "".join(t[1] for t in onsite).encode()
+        oc_ = _f64([t[2] for t in onsite])
+        bi = np.array([t[0] for t in bonds], dtype=np.int32)
+        bj = np.array([t[1] for t in bonds], dtype=np.int32)
+        pi = "".join(t[2] for t in bonds).encode()
+        pj = "".join(t[3] for t in bonds).encode()
+        bc = _f64([t[4] for t in bonds])
+        cr = (rmc_op_tag * max(1, len(carry)))(*[rmc_op_tag(s, p.encode()) for s, p in carry])
+        out = ctypes.c_void_p()
+        ip = ctypes.POINTER(ctypes.c_int)
+        self._check(self.lib.rmc_build_leaf_pauli(
+            self.h, L, k, len(onsite), os_.ctypes.data_as(ip), op_, _dptr(oc_), len(bonds), bi.ctypes.data_as(ip),
+            bj.ctypes.data_as(ip), pi, pj, _dptr(bc), len(carry), cr, ctypes.byref(out)))
+        return Block(self, out.value)
+
+    def couple(self, A: Block, B: Block, terms, k_keep: int, carry=(), top: bool = False,
+               allow_noconv: bool = False) -> Block:
+        tt = (rmc_term * max(1, len(terms)))(*[rmc_term(c, a, b) for c, a, b in terms])
+        cc = (rmc_carry * max(1, len(carry)))(*[rmc_carry(s, o) for s, o in carry])
+        out = ctypes.c_void_p()
+        st = self.lib.rmc_couple(self.h, A.handle, B.handle, tt, len(terms), k_keep, cc, len(carry),
+                                 RMC_COUPLE_TOP if top else 0, ctypes.byref(out))
+        self._check(st, allow=(RMC_ERR_NOCONV,) if allow_noconv else ())
+        return Block(self, out.value)
+
+    def lowest(self, blk: Block, q: int, with_states: bool = False):
+        k, _, rows, _ = blk.info()
+        qq = min(q, k)
+        E = np.empty(qq)
+        C = np.empty((rows, qq)) if (with_states and rows) else None
+        keff = ctypes.c_int()
+        self._check(self.lib.rmc_lowest(self.h, blk.handle, q, _dptr(E), _dptr(C) if C is not None else None,
+                                        ctypes.byref(keff)))
+        return (E, C) if with_states else E
+
+    def block_import(self, E, ops=(), tags=(), basis=None) -> Block:
+        E = _f64(E)
+        k = len(E)
+        opsa = _f64(np.array(ops).reshape(len(ops), k, k)) if len(ops) else np.zeros((1, k, k))
+        tg = (rmc_op_tag * max(1, len(ops)))(*[rmc_op_tag(s, p.encode()) for s, p in tags]) if tags else None
+        rows = 0 if basis is None else basis.shape[1]
+        bs = _f64(basis) if basis is not None else None
+        out = ctypes.c_void_p()
+        self._check(self.lib.rmc_block_import(self.h, k, _dptr(E), len(ops), _dptr(opsa), tg, rows,
+                                              _dptr(bs) if bs is not None else None, ctypes.byref(out)))
+        return Block(self, out.value)
+
+    def solve_chain(self, chain) -> np.ndarray:
+        """Algorithm 1 over a chain description (``instances.Chain``-like):
+        returns the lowest q energies."""
+        ons, bnd = chain.onsite, chain.bonds
+        ip = ctypes.POINTER(ctypes.c_int)
+        os_ = np.array([t[0] for t in ons], dtype=np.int32)
+        bi = np.array([t[0] for t in bnd], dtype=np.int32)
+        bj = np.array([t[1] for t in bnd], dtype=np.int32)
+        E = np.full(chain.q, np.nan)
+        st = self.lib.rmc_solve_chain(
+            self.h, chain.n_sites, chain.leaf_sites, chain.k, chain.q, len(ons), os_.ctypes.data_as(ip),
+            "".join(t[1] for t in ons).encode(), _dptr(_f64([t[2] for t in ons])), len(bnd),
+            bi.ctypes.data_as(ip), bj.ctypes.data_as(ip), "".join(t[2] for t in bnd).encode(),
+            "".join(t[3] for t in bnd).encode(), _dptr(_f64([t[4] for t in bnd])), _dptr(E))
+        self._check(st)
+        return E
+
+    # ---- kernel-level entry points (device pointers) -------------------------
+    def kron_matvec(self, dtype: int, kA: int, kB: int, n_ops: int, nv: int, EA: int, EB: int, A: int, B: int,
+                    coef, X: int, Y: int, Z: int = 0, alpha: float = 1.0, beta: float = 0.0, gamma: float = 0.0):
+        c = _f64(coef if len(coef) else [0.0])
+        self._check(self.lib.rmc_kron_matvec(self.h, dtype, kA, kB, n_ops, nv, EA, EB, A or None, B or None,
+                                             _dptr(c), X, Y, Z or None, alpha, beta, gamma))
+
+    def syev(self, m: int, S: int, w: int, V: int):
+        self._check(self.lib.rmc_syev(self.h, m, S, w, V))
+
+    def rotate_op(self, side: int, kA: int, kB: int, kr: int, C: int, o: int, out: int):
+        self._check(self.lib.rmc_rotate_op(self.h, side, kA, kB, kr, C, o, out))

@@ -1,0 +1,649 @@
+// Device kernels of the merge step (Algorithm 1, inner loop) and the leaf
+// build (Algorithm 1, first step).  Every kernel here is launched by the host
+// driver in rmc.cu; see the comments there for the order.
+#pragma once
+
+#include "common.cuh"
+#include "gemm.cuh"
+
+namespace rmc {
+
+constexpr int kMaxOps = 32;        // carried operators / coupling terms per merge
+constexpr int kMaxSmallDim = 160;  // Jacobi eigensolver: matrix held in shared memory
+
+struct Coefs {
+  double c[kMaxOps];
+};
+
+// ---------------------------------------------------------------------------
+// Kronecker-form product with H_eff (Eq. (7)) in two GEMM stages:
+//   stage 1: T[(j, a), (v, b)] = sum_b' X[v][a][b'] * B_j[b][b']
+//   stage 2: Y[v][a][b] = alpha * ( (EA[a] + EB[b]) X[v][a][b]
+//                                   + sum_{j, a'} coef_j A_j[a][a'] T[(j, a'), (v, b)] )
+//                         + beta * X[v][a][b] + gamma * Z[v][a][b]
+// Stage 2 contracts over (j, a') at once with Acat[a][(j, a')] = coef_j A_j[a][a'].
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void build_acat_kernel(const T* __restrict__ A, Coefs coef, int kA, int n_ops, T* __restrict__ Acat) {
+  const long total = (long)kA * n_ops * kA;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / (n_ops * kA));
+    const int r = (int)(e % (n_ops * kA));
+    const int j = r / kA, ap = r % kA;
+    Acat[e] = (T)coef.c[j] * A[((long)j * kA + a) * kA + ap];
+  }
+}
+
+template <typename T>
+struct EpiKron1 {  // m = v*kA + a, n = j*kB + b  ->  T[((j*kA + a)*nv + v)*kB + b]
+  T* Tbuf;
+  int kA, kB, nv;
+  __device__ void operator()(int, int, int m, int n, T acc) const {
+    const int v = m / kA, a = m % kA, j = n / kB, b = n % kB;
+    Tbuf[(((long)j * kA + a) * nv + v) * kB + b] = acc;
+  }
+};
+
+template <typename T>
+struct EpiKron2 {  // m = a, n = v*kB + b
+  const T* X;
+  const T* Z;
+  const T* EA;
+  const T* EB;
+  T* Y;
+  int kA, kB;
+  T alpha, beta, gamma;
+  __device__ void operator()(int, int, int m, int n, T acc) const {
+    const int v = n / kB, b = n % kB;
+    const long idx = ((long)v * kA + m) * kB + b;
+    const T x = X[idx];
+    T y = alpha * (acc + (EA[m] + EB[b]) * x) + beta * x;
+    if (gamma != T(0)) y += gamma * Z[idx];
+    Y[idx] = y;
+  }
+};
+
+// Y = alpha * acc + beta * Src (Src may alias nothing written by the GEMM).
+template <typename T>
+struct EpiAxpby {
+  T* C;
+  const T* Src;
+  long ldc, lds;
+  long batch_stride_c, batch_stride_s;
+  T alpha, beta;
+  __device__ void operator()(int bt, int, int m, int n, T acc) const {
+    T v = alpha * acc;
+    if (beta != T(0)) v += beta * Src[(long)bt * batch_stride_s + (long)m * lds + n];
+    C[(long)bt * batch_stride_c + (long)m * ldc + n] = v;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers
+// ---------------------------------------------------------------------------
+
+template <typename TO, typename TI>
+__global__ void convert_kernel(const TI* __restrict__ in, TO* __restrict__ out, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    out[e] = (TO)in[e];
+}
+
+// Diagonal of H_eff (Eq. (7)): D[a*kB + b] = EA[a] + EB[b] + sum_j coef_j A_j[a][a] B_j[b][b].
+__global__ void diag_kernel(const double* __restrict__ EA, const double* __restrict__ EB,
+                            const double* __restrict__ A, const double* __restrict__ B, Coefs coef,
+                            int n_ops, int kA, int kB, double* __restrict__ D) {
+  const long n = (long)kA * kB;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / kB), b = (int)(e % kB);
+    double d = EA[a] + EB[b];
+    for (int j = 0; j < n_ops; ++j)
+      d += coef.c[j] * A[((long)j * kA + a) * kA + a] * B[((long)j * kB + b) * kB + b];
+    D[e] = d;
+  }
+}
+
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  unsigned long long u = __double_as_longlong(x);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// One CTA (1024 threads): the b smallest entries of D (ties broken by index),
+// written as idx[0..b-1] in ascending (D, index) order; also min and max of D.
+// Radix select on order-preserving 64-bit keys, stable compaction, bitonic
+// sort of the selected pairs.  b <= 1024.
+__global__ void __launch_bounds__(1024) select_smallest_kernel(const double* __restrict__ D, long n, int b,
+                                                               int* __restrict__ idx, double* __restrict__ dminmax) {
+  __shared__ unsigned int hist[256];
+  __shared__ unsigned long long s_prefix, s_mask;
+  __shared__ long s_need;
+  __shared__ unsigned long long skey[1024];
+  __shared__ int sidx[1024];
+  __shared__ int s_take_less, s_take_eq;
+  __shared__ double red[32];
+  const int tid = threadIdx.x;
+
+  double lo = INFINITY, hi = -INFINITY;
+  for (long i = tid; i < n; i += blockDim.x) { lo = fmin(lo, D[i]); hi = fmax(hi, D[i]); }
+  hi = block_max(hi, red);
+  lo = -block_max(-lo, red);
+  if (tid == 0) { dminmax[0] = lo; dminmax[1] = hi; s_prefix = 0; s_mask = 0; s_need = b; }
+  __syncthreads();
+
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const unsigned long long pre = s_prefix, msk = s_mask;
+    for (long i = tid; i < n; i += blockDim.x) {
+      const unsigned long long k = order_key(D[i]);
+      if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long need = s_need, cum = 0;
+      int d = 0;
+      for (; d < 256; ++d) {
+        if (cum + (long)hist[d] >= need) break;
+        cum += hist[d];
+      }
+      s_need = need - cum;
+      s_prefix = pre | ((unsigned long long)d << shift);
+      s_mask = msk | (0xFFull << shift);
+    }
+    __syncthreads();
+  }
+  const unsigned long long kstar = s_prefix;
+  const long need_eq = s_need;  // equal keys to take (>= 1)
+  // stable compaction in index order
+  if (tid == 0) { s_take_less = 0; s_take_eq = 0; }
+  __syncthreads();
+  __shared__ int wsum_l[32], wsum_e[32];
+  for (long base = 0; base < n; base += blockDim.x) {
+    const long i = base + tid;
+    int isl = 0, ise = 0;
+    unsigned long long k = 0;
+    if (i < n) {
+      k = order_key(D[i]);
+      isl = k < kstar;
+      ise = k == kstar;
+    }
+    // block exclusive scans of isl and ise
+    const int lane = tid & 31, wid = tid >> 5;
+    int xl = isl, xe = ise;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int yl = __shfl_up_sync(0xffffffffu, xl, o), ye = __shfl_up_sync(0xffffffffu, xe, o);
+      if (lane >= o) { xl += yl; xe += ye; }
+    }
+    if (lane == 31) { wsum_l[wid] = xl; wsum_e[wid] = xe; }
+    __syncthreads();
+    if (wid == 0) {
+      int vl = wsum_l[lane], ve = wsum_e[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int yl = __shfl_up_sync(0xffffffffu, vl, o), ye = __shfl_up_sync(0xffffffffu, ve, o);
+        if (lane >= o) { vl += yl; ve += ye; }
+      }
+      wsum_l[lane] = vl;
+      wsum_e[lane] = ve;
+    }
+    __syncthreads();
+    const int exl = xl - isl + (wid ? wsum_l[wid - 1] : 0);
+    const int exe = xe - ise + (wid ? wsum_e[wid - 1] : 0);
+    const int tl = s_take_less, te = s_take_eq;
+    __syncthreads();
+    // positions: less-than keys are all taken; equal keys only the first need_eq
+    if (isl) {
+      const int slot = tl + exl;  // provisional among "less"
+      skey[slot] = k;            // less keys never exceed b - need_eq slots
+      sidx[slot] = (int)i;
+    }
+    __syncthreads();
+    if (ise && (long)(te + exe) < need_eq) {
+      const int slot = (b - (int)need_eq) + te + exe;
+      skey[slot] = k;
+      sidx[slot] = (int)i;
+    }
+    __syncthreads();
+    if (tid == 0) { s_take_less = tl + wsum_l[31]; s_take_eq = te + wsum_e[31]; }
+    __syncthreads();
+  }
+  // bitonic sort of (key, index) over the next power of two >= b
+  int P = 1;
+  while (P < b) P <<= 1;
+  for (int i = b + tid; i < P; i += blockDim.x) { skey[i] = ~0ull; sidx[i] = 0x7fffffff; }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < P; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = ((i & size) == 0);
+          const bool gt = (skey[i] > skey[j]) || (skey[i] == skey[j] && sidx[i] > sidx[j]);
+          if (gt == up) {
+            unsigned long long tk = skey[i]; skey[i] = skey[j]; skey[j] = tk;
+            int ti = sidx[i]; sidx[i] = sidx[j]; sidx[j] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < b; i += blockDim.x) idx[i] = sidx[i];
+}
+
+// X[i] = e_{idx[i]}  (vector-major, X zeroed by the caller)
+template <typename T>
+__global__ void unit_vectors_kernel(const int* __restrict__ idx, int b, long n, T* __restrict__ X) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < b) X[(long)i * n + idx[i]] = T(1);
+}
+
+// Normalise each vector (one CTA per vector); records the norms.
+template <typename T>
+__global__ void normalize_kernel(T* __restrict__ X, long n, T* __restrict__ norms) {
+  __shared__ T red[32];
+  T* x = X + (long)blockIdx.x * n;
+  T s = 0;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
+  s = block_sum(s, red);
+  const T nr = sqrt(s);
+  const T inv = nr > T(0) ? T(1) / nr : T(0);
+  for (long i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+  if (threadIdx.x == 0 && norms) norms[blockIdx.x] = nr;
+}
+
+// Residual norms of Ritz pairs, rn[i] = ||HX_i - theta_i X_i|| (one CTA per
+// vector, warp-shuffle block reduction), and the count of i < k_conv with
+// rn[i] > tol * max(1, |theta_i|) into status[0] (zeroed by the caller).
+template <typename T>
+__global__ void residual_kernel(const T* __restrict__ X, const T* __restrict__ HX, const T* __restrict__ theta,
+                                long n, int k_conv, double tol, double* __restrict__ rn, int* __restrict__ status) {
+  __shared__ T red[32];
+  const int i = blockIdx.x;
+  const T* x = X + (long)i * n;
+  const T* hx = HX + (long)i * n;
+  const T th = theta[i];
+  T s = 0;
+  for (long r = threadIdx.x; r < n; r += blockDim.x) {
+    const T d = hx[r] - th * x[r];
+    s += d * d;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double r = sqrt((double)s);
+    rn[i] = r;
+    if (i < k_conv && !(r <= tol * fmax(1.0, fabs((double)th)))) atomicAdd(status, 1);
+  }
+}
+
+// Flip each vector so that its entry of largest magnitude (first one on exact
+// ties) is positive (one CTA per vector).
+__global__ void gauge_kernel(double* __restrict__ C, long n) {
+  __shared__ double sv[32];
+  __shared__ long si[32];
+  double* c = C + (long)blockIdx.x * n;
+  double best = -1.0;
+  long bi = 0x7fffffffffffffffL;
+  for (long r = threadIdx.x; r < n; r += blockDim.x) {
+    const double a = fabs(c[r]);
+    if (a > best) { best = a; bi = r; }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { sv[wid] = best; si[wid] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 1; w < nw; ++w)
+      if (sv[w] > sv[0] || (sv[w] == sv[0] && si[w] < si[0])) { sv[0] = sv[w]; si[0] = si[w]; }
+  }
+  __syncthreads();
+  const bool flip = c[si[0]] < 0.0;
+  __syncthreads();
+  if (flip)
+    for (long r = threadIdx.x; r < n; r += blockDim.x) c[r] = -c[r];
+}
+
+// ---------------------------------------------------------------------------
+// Small dense symmetric eigensolver, one CTA: cyclic parallel Jacobi in FP32
+// with round-robin pairing (all m(m-1)/2 pairs once per sweep, m/2 disjoint
+// rotations per round; each 2x2 block of A updated by one thread as
+// J_k^T A_{kl} J_l).  Eigenvalues ascending into w, eigenvectors as columns of
+// the row-major m x m V.  m <= kMaxSmallDim.  status[0] += 1 if the sweep cap
+// was hit before the off-diagonal norm fell below 1e-6 ||A||_F.
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(512) jacobi_kernel(const TI* __restrict__ S, int m, TO* __restrict__ w,
+                                                     TO* __restrict__ V, int* __restrict__ status, int max_sweeps) {
+  extern __shared__ float smem[];
+  const int mm = (m + 1) & ~1;  // even
+  float* A = smem;              // mm x mm
+  float* Vs = A + mm * mm;      // m x mm
+  float* cs = Vs + m * mm;      // mm/2
+  float* sn = cs + mm / 2;
+  int* P = (int*)(sn + mm / 2);
+  int* Q = P + mm / 2;
+  __shared__ float red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int e = tid; e < mm * mm; e += nt) {
+    const int i = e / mm, j = e % mm;
+    float v = 0.f;
+    if (i < m && j < m) v = (float)(0.5 * ((double)S[i * m + j] + (double)S[j * m + i]));
+    A[e] = v;
+  }
+  for (int e = tid; e < m * mm; e += nt) Vs[e] = ((e / mm) == (e % mm)) ? 1.f : 0.f;
+  __syncthreads();
+  float fro = 0.f;
+  for (int e = tid; e < m * mm; e += nt) {
+    const int i = e / mm, j = e % mm;
+    if (j < m) fro += A[i * mm + j] * A[i * mm + j];
+  }
+  fro = sqrtf(block_sum(fro, red));
+  const float target = 1e-6f * fro;
+
+  const int half = mm / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float off = 0.f;
+    for (int e = tid; e < m * mm; e += nt) {
+      const int i = e / mm, j = e % mm;
+      if (j < m && j != i) off += A[i * mm + j] * A[i * mm + j];
+    }
+    off = sqrtf(block_sum(off, red));
+    if (off <= target || fro == 0.f) break;
+    for (int r = 0; r < mm - 1; ++r) {
+      for (int k = tid; k < half; k += nt) {
+        int p, q;
+        if (k == 0) { p = r; q = mm - 1; }
+        else { p = (r + k) % (mm - 1); q = (r - k + mm - 1) % (mm - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        float c = 1.f, s = 0.f;
+        if (q < m) {
+          const float apq = A[p * mm + q];
+          if (apq != 0.f) {
+            const float app = A[p * mm + p], aqq = A[q * mm + q];
+            const float tau = (aqq - app) / (2.f * apq);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            s = t * c;
+          }
+        }
+        cs[k] = c; sn[k] = s; P[k] = p; Q[k] = q;
+      }
+      __syncthreads();
+      // A <- J^T A J, block by block
+      for (int e = tid; e < half * half; e += nt) {
+        const int k = e / half, l = e % half;
+        const int pk = P[k], qk = Q[k], pl = P[l], ql = Q[l];
+        const float ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
+        const float a00 = A[pk * mm + pl], a01 = A[pk * mm + ql];
+        const float a10 = A[qk * mm + pl], a11 = A[qk * mm + ql];
+        // rows: J_k^T = [[c, -s], [s, c]]
+        const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
+        const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
+        // cols: J_l = [[c, s], [-s, c]]
+        float n00 = b00 * cl - b01 * sl, n01 = b00 * sl + b01 * cl;
+        float n10 = b10 * cl - b11 * sl, n11 = b10 * sl + b11 * cl;
+        if (k == l) { n01 = 0.f; n10 = 0.f; }
+        A[pk * mm + pl] = n00; A[pk * mm + ql] = n01;
+        A[qk * mm + pl] = n10; A[qk * mm + ql] = n11;
+      }
+      // V <- V J
+      for (int e = tid; e < m * half; e += nt) {
+        const int row = e / half, l = e % half;
+        const int pl = P[l], ql = Q[l];
+        const float c = cs[l], s = sn[l];
+        const float vp = Vs[row * mm + pl], vq = Vs[row * mm + ql];
+        Vs[row * mm + pl] = c * vp - s * vq;
+        Vs[row * mm + ql] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  if (sweep == max_sweeps && tid == 0 && status) atomicAdd(status, 1);
+  // sort eigenvalues ascending (rank sort, ties by index)
+  for (int i = tid; i < m; i += nt) {
+    const float di = A[i * mm + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const float dj = A[j * mm + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    w[rank] = (TO)di;
+    for (int row = 0; row < m; ++row) V[row * m + rank] = (TO)Vs[row * mm + i];
+  }
+}
+
+inline size_t jacobi_smem_bytes(int m) {
+  const int mm = (m + 1) & ~1;
+  return sizeof(float) * ((size_t)mm * mm + (size_t)m * mm + mm) + sizeof(int) * mm;
+}
+
+// Ogita-Aishima refinement (Japan J. Indust. Appl. Math. 35, 2018), the step
+// between the three products: given R = I - V^T V and Sp = V^T A V (m x m,
+// FP64), form lambda_i = Sp_ii / (1 - R_ii) and the correction E with
+// E_ij = (Sp_ij + lambda_j R_ij) / (lambda_j - lambda_i) where
+// |lambda_i - lambda_j| > delta and R_ij / 2 otherwise (clustered pairs are
+// only re-orthogonalised), delta = 2 (||Sp - diag(lambda)||_F + ||A||_F ||R||_F).
+// One CTA.  R is overwritten by E.
+__global__ void oa_correction_kernel(double* __restrict__ R, const double* __restrict__ Sp,
+                                     const double* __restrict__ A, int m, double* __restrict__ lam,
+                                     int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[32];
+  extern __shared__ double sl[];  // m
+  const int tid = threadIdx.x;
+  double an = 0.0;
+  for (int e = tid; e < m * m; e += blockDim.x) an += A[e] * A[e];
+  const double Anorm = sqrt(block_sum(an, red));
+  for (int i = tid; i < m; i += blockDim.x) sl[i] = Sp[i * m + i] / (1.0 - R[i * m + i]);
+  __syncthreads();
+  double off = 0.0, rr = 0.0;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    const double d = Sp[e] - (i == j ? sl[i] : 0.0);
+    off += d * d;
+    rr += R[e] * R[e];
+  }
+  off = block_sum(off, red);
+  rr = block_sum(rr, red);
+  const double delta = 2.0 * (sqrt(off) + Anorm * sqrt(rr));
+  double emax = 0.0;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    const double r = R[e];
+    double E;
+    if (i != j && fabs(sl[i] - sl[j]) > delta) E = (Sp[e] + sl[j] * r) / (sl[j] - sl[i]);
+    else E = 0.5 * r;
+    R[e] = E;
+    emax = fmax(emax, fabs(E));
+  }
+  emax = block_max(emax, red);
+  for (int i = tid; i < m; i += blockDim.x) lam[i] = sl[i];
+  // a correction at the rounding level of FP64 leaves V unchanged: stop
+  if (tid == 0 && emax <= 4e-16) *done = 1;
+}
+
+// dst = src (m x m) unless *skip
+__global__ void copy_unless_kernel(const double* __restrict__ src, double* __restrict__ dst, int count,
+                                   const int* __restrict__ skip) {
+  if (*skip) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) dst[e] = src[e];
+}
+
+// R = I - G (in place, m x m) unless *skip
+__global__ void identity_minus_kernel(double* __restrict__ G, int m, const int* __restrict__ skip) {
+  if (*skip) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)
+    G[e] = ((e / m) == (e % m) ? 1.0 : 0.0) - G[e];
+}
+
+// Sort eigenpairs ascending by lam (one CTA, rank sort): w[rank]=lam[i],
+// Vout[:, rank] = Vin[:, i].
+__global__ void sort_pairs_kernel(const double* __restrict__ lam, const double* __restrict__ Vin, int m,
+                                  double* __restrict__ w, double* __restrict__ Vout) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double li = lam[i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) rank += (lam[j] < li) || (lam[j] == li && j < i);
+    w[rank] = li;
+    for (int r = 0; r < m; ++r) Vout[r * m + rank] = Vin[r * m + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky G + shift*max(diag) I = L L^T and L^{-1}, one CTA, computed in TC.
+// One m x m array in shared memory: L in the lower triangle (with diagonal),
+// the strict lower part of L^{-1} stored transposed in the strict upper
+// triangle (its diagonal is 1 / L_ii).  Output Linv (row-major m x m, lower
+// triangular) in TO.  status[0] += 1 when a pivot was not positive (the pivot
+// is then clamped).
+// ---------------------------------------------------------------------------
+template <typename TC, typename TI, typename TO>
+__global__ void __launch_bounds__(512) cholinv_kernel(const TI* __restrict__ G, int m, double shift,
+                                                      TO* __restrict__ Linv, int* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  TC* L = (TC*)smem_raw;  // m x m
+  __shared__ TC red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  TC dmax = 0;
+  for (int i = tid; i < m; i += nt) dmax = fmax(dmax, (TC)G[i * m + i]);
+  dmax = block_max(dmax, red);
+  const TC sh = (TC)shift * dmax;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, j = e % m;
+    L[e] = (j <= i) ? (TC)(0.5 * ((double)G[i * m + j] + (double)G[j * m + i])) + (i == j ? sh : TC(0)) : TC(0);
+  }
+  __syncthreads();
+  const TC tiny = dmax * (TC)1e-30 + (TC)(sizeof(TC) == 4 ? 1e-37 : 1e-300);
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      TC d = L[j * m + j];
+      if (!(d > tiny)) {
+        if (status) atomicAdd(status, 1);
+        d = fmax(dmax, tiny) * (TC)1e-12;
+      }
+      L[j * m + j] = sqrt(d);
+    }
+    __syncthreads();
+    const TC ljj = L[j * m + j];
+    for (int i = j + 1 + tid; i < m; i += nt) L[i * m + j] /= ljj;
+    __syncthreads();
+    const int rem = m - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+      if (k <= i) L[i * m + k] -= L[i * m + j] * L[k * m + j];
+    }
+    __syncthreads();
+  }
+  // forward substitution row by row: for c < i,
+  //   Li[i][c] = -(sum_{t=c}^{i-1} L[i][t] Li[t][c]) / L[i][i],  Li[t][t] = 1 / L[t][t],
+  // with Li[t][c] (c < t) kept at L[c*m + t].
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int i = 1; i < m; ++i) {
+    for (int c = wid; c < i; c += nw) {
+      TC s = 0;
+      for (int t = c + lane; t < i; t += 32) {
+        const TC lit = (t == c) ? TC(1) / L[t * m + t] : L[c * m + t];
+        s += L[i * m + t] * lit;
+      }
+      s = warp_sum(s);
+      if (lane == 0) L[c * m + i] = -s / L[i * m + i];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, c = e % m;
+    TO v = TO(0);
+    if (c == i) v = (TO)(TC(1) / L[i * m + i]);
+    else if (c < i) v = (TO)L[c * m + i];
+    Linv[e] = v;
+  }
+}
+
+inline size_t cholinv_smem_bytes(int m, size_t elt) { return (size_t)m * m * elt; }
+
+// out[i][r] = V[r][i] for i < k: the first k columns of a row-major m x m
+// eigenvector matrix as k vectors of length m.
+template <typename T>
+__global__ void columns_to_vectors_kernel(const T* __restrict__ V, int m, int k, T* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * m; e += gridDim.x * blockDim.x) {
+    const int i = e / m, r = e % m;
+    out[e] = V[r * m + i];
+  }
+}
+
+// out = a1 * P + a2 * Q (elementwise)
+template <typename T>
+__global__ void axpby_kernel(const T* __restrict__ P, const T* __restrict__ Q, long tot, T a1, T a2, T* __restrict__ out) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    out[e] = a1 * P[e] + a2 * Q[e];
+}
+
+// F^T for the first-order second Cholesky-QR pass: G = I + E  =>  R ~ I + F,
+// F upper triangular with F_ij = E_ij (i < j), F_ii = E_ii / 2; returns
+// W = F^T (lower triangular) so that X_new = X - W X.
+__global__ void cholqr_first_order_kernel(const double* __restrict__ G, int m, double* __restrict__ W) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e / m, j = e % m;  // W[i][j] = F[j][i]
+    double v = 0.0;
+    if (j < i) v = 0.5 * (G[j * m + i] + G[i * m + j]);
+    else if (j == i) v = 0.5 * (G[i * m + i] - 1.0);
+    W[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf build from Pauli terms (Algorithm 1, first step): one CTA; each thread
+// owns columns c of the D x D matrix and adds every term's single nonzero in
+// that column.  Site s of an L-site block is bit (L-1-s) of the index (site 0
+// is the most significant tensor factor).  Pauli codes: 1 = X, 2 = Y (carried
+// as iY = [[0,1],[-1,0]]), 3 = Z.  A term is coef * P_{s0} P_{s1} (s1 < 0 for
+// an on-site term).
+// ---------------------------------------------------------------------------
+struct PauliTerm {
+  int s0, s1;
+  int p0, p1;
+  double coef;
+};
+
+__device__ __forceinline__ double pauli_apply(int code, int bit, int* flip) {
+  // returns the factor of <r|P|c> for the column bit value `bit`; sets *flip
+  if (code == 1) { *flip = 1; return 1.0; }
+  if (code == 2) { *flip = 1; return bit ? 1.0 : -1.0; }  // iY|0> = -|1>, iY|1> = |0>
+  *flip = 0;
+  return bit ? -1.0 : 1.0;                                // Z
+}
+
+__global__ void pauli_matrix_kernel(const PauliTerm* __restrict__ terms, int n_terms, int L,
+                                    double* __restrict__ M) {
+  const int D = 1 << L;
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < D * D; e += blockDim.x * gridDim.x) M[e] = 0.0;
+  __syncthreads();
+  for (int c = threadIdx.x + blockIdx.x * blockDim.x; c < D; c += blockDim.x * gridDim.x) {
+    for (int t = 0; t < n_terms; ++t) {
+      const PauliTerm pt = terms[t];
+      int r = c;
+      double v = pt.coef;
+      int flip;
+      const int b0 = L - 1 - pt.s0;
+      v *= pauli_apply(pt.p0, (c >> b0) & 1, &flip);
+      if (flip) r ^= (1 << b0);
+      if (pt.s1 >= 0) {
+        const int b1 = L - 1 - pt.s1;
+        v *= pauli_apply(pt.p1, (c >> b1) & 1, &flip);
+        if (flip) r ^= (1 << b1);
+      }
+      M[(long)r * D + c] += v;
+    }
+  }
+}
+
+}  // namespace rmc

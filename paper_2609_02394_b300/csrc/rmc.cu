@@ -1,0 +1,1265 @@
+// Host driver and C ABI of the recursive module-coupling eigensolver.
+//
+// Algorithm 1 of the paper, B300-native:
+//   * rmc_build_leaf[_pauli]  leaf module: dense H on the device, FP64-accurate
+//                             small eigensolve, projected carried operators.
+//   * rmc_couple              one merge: diagonal + start block, Chebyshev-
+//                             filtered subspace iteration on the Kronecker-form
+//                             product (working precision FP64 or FP32), FP64
+//                             finalisation (Cholesky-QR, Rayleigh-Ritz with
+//                             refined eigenvectors), degenerate cut, gauge,
+//                             rotation of the carried operators.
+//   * rmc_solve_chain         the recursion loop with homogeneous reuse.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/rmc.h"
+#include "common.cuh"
+#include "gemm.cuh"
+#include "kernels.cuh"
+
+using namespace rmc;
+
+struct rmc_block {
+  int k = 0;          // kept states
+  int n_ops = 0;      // carried operators
+  int rows = 0;       // basis rows (D for a leaf, kA*kB for a merge; 0 = none)
+  double* E = nullptr;      // k
+  double* ops = nullptr;    // n_ops * k * k
+  double* basis = nullptr;  // k vectors of `rows` (vector-major)
+  std::vector<rmc_op_tag> tags;
+  std::vector<double> opnorm;  // upper bound of each operator's 2-norm
+  size_t bytes = 0;
+};
+
+struct rmc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaMemPool_t pool = nullptr;
+  size_t budget = 0;
+  size_t in_use = 0;
+  std::map<void*, size_t> live;
+  rmc_config cfg{};
+  std::string err;
+  uint64_t launches = 0, iterations = 0;
+  int* d_status = nullptr;      // device scratch ints
+  double* h_pinned = nullptr;   // pinned host staging (status + thetas)
+  std::set<rmc_block*> blocks;
+};
+
+namespace {
+
+constexpr size_t kPinnedDoubles = 4096;
+
+rmc_status fail(rmc_ctx* ctx, rmc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return st;
+}
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(ctx, RMC_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,  \
+                                       cudaGetErrorString(e_));                                       \
+  } while (0)
+#define CKL()                                                                                         \
+  do {                                                                                                \
+    ctx->launches++;                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                              \
+    if (e_ != cudaSuccess) return fail(ctx, RMC_ERR_CUDA, "%s:%d launch: %s", __FILE__, __LINE__,     \
+                                       cudaGetErrorString(e_));                                       \
+  } while (0)
+#define TRY(x)                          \
+  do {                                  \
+    rmc_status s_ = (x);                \
+    if (s_ != RMC_OK) return s_;        \
+  } while (0)
+
+rmc_status dalloc(rmc_ctx* ctx, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  if (ctx->in_use + bytes > ctx->budget)
+    return fail(ctx, RMC_ERR_NOMEM, "device-memory budget exceeded: need %zu more bytes, %zu of %zu in use",
+                bytes, ctx->in_use, ctx->budget);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, RMC_ERR_NOMEM, "cudaMallocFromPoolAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->in_use += bytes;
+  ctx->live[*p] = bytes;
+  return RMC_OK;
+}
+
+void dfree(rmc_ctx* ctx, void* p) {
+  if (!p) return;
+  auto it = ctx->live.find(p);
+  if (it != ctx->live.end()) {
+    ctx->in_use -= it->second;
+    ctx->live.erase(it);
+  }
+  cudaFreeAsync(p, ctx->stream);
+}
+
+// Scoped workspace: every allocation is released when it goes out of scope.
+struct Workspace {
+  rmc_ctx* ctx;
+  std::vector<void*> ptrs;
+  explicit Workspace(rmc_ctx* c) : ctx(c) {}
+  ~Workspace() {
+    for (void* p : ptrs) dfree(ctx, p);
+  }
+  template <typename T>
+  rmc_status get(T** p, size_t count) {
+    void* q = nullptr;
+    TRY(dalloc(ctx, &q, count * sizeof(T)));
+    ptrs.push_back(q);
+    *p = (T*)q;
+    return RMC_OK;
+  }
+};
+
+inline unsigned grid1d(long n, int threads = 256) { return (unsigned)std::min<long>(std::max<long>(1, (n + threads - 1) / threads), 148 * 16); }
+
+// ---------------------------------------------------------------------------
+// GEMM front ends on vector-major blocks (a block of nv vectors of length n is
+// a row-major nv x n matrix).
+// ---------------------------------------------------------------------------
+template <typename T, bool TA, bool TB, class Epi>
+void gemm_big(const T* A, const T* B, const GemmShape& s, int batches, const Epi& epi, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) launch_gemm<T, 64, 64, 16, 4, 4, TA, TB>(A, B, s, batches, epi, st);
+  else launch_gemm<T, 64, 64, 8, 4, 4, TA, TB>(A, B, s, batches, epi, st);
+}
+template <typename T, bool TA, bool TB, class Epi>
+void gemm_small(const T* A, const T* B, const GemmShape& s, int batches, const Epi& epi, cudaStream_t st) {
+  launch_gemm<T, 16, 16, 16, 1, 1, TA, TB>(A, B, s, batches, epi, st);
+}
+
+// G (nv1 x nv2) = X1 X2^T, contraction over n, deterministic split-K.
+template <typename T>
+rmc_status gram(rmc_ctx* ctx, Workspace& ws, const T* X1, int nv1, const T* X2, int nv2, long n, T* G,
+                bool symmetrize) {
+  const int tiles = (int)(ceil_div(nv1, 64) * ceil_div(nv2, 64));
+  int splits = (int)std::min<long>(std::max<long>(1, n / 128), std::max(1, 296 / tiles));
+  splits = std::min(splits, 64);
+  T* P = nullptr;
+  TRY(ws.get(&P, (size_t)splits * nv1 * nv2));
+  GemmShape s{nv1, nv2, (int)n, n, n, 0, 0, splits};
+  EpiStore<T> epi{P, nv2, 0, (long)nv1 * nv2, T(1), T(0)};
+  if (nv1 <= 32 && nv2 <= 32) gemm_small<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
+  else gemm_big<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
+  CKL();
+  reduce_splits_kernel<T><<<grid1d((long)nv1 * nv2), 256, 0, ctx->stream>>>(P, splits, (long)nv1 * nv2, nv1, nv2, G,
+                                                                             nv2, T(1), T(0), symmetrize ? 1 : 0);
+  CKL();
+  return RMC_OK;
+}
+
+// Out (nvo x n) = alpha * op(W) X + beta * Src; op(W) = W (nvo x nvi) or W^T
+// (W stored nvi x nvo).
+template <typename T>
+rmc_status combine(rmc_ctx* ctx, const T* W, bool transW, int nvo, int nvi, const T* X, long n, T* Out, T alpha,
+                   T beta, const T* Src) {
+  GemmShape s{nvo, (int)n, nvi, transW ? nvo : nvi, n, 0, 0, 1};
+  EpiAxpby<T> epi{Out, Src, n, n, 0, 0, alpha, beta};
+  if (transW) gemm_big<T, true, false>(W, X, s, 1, epi, ctx->stream);
+  else gemm_big<T, false, false>(W, X, s, 1, epi, ctx->stream);
+  CKL();
+  return RMC_OK;
+}
+
+// C (m x m) = alpha op(A) op(B) + beta Src for the small Rayleigh-Ritz products.
+template <typename T, bool TA, bool TB>
+rmc_status small_mm(rmc_ctx* ctx, const T* A, const T* B, int m, T* C, T alpha, T beta, const T* Src) {
+  GemmShape s{m, m, m, m, m, 0, 0, 1};
+  EpiAxpby<T> epi{C, Src, m, m, 0, 0, alpha, beta};
+  gemm_small<T, TA, TB>(A, B, s, 1, epi, ctx->stream);
+  CKL();
+  return RMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kronecker-form product with the effective Hamiltonian (Eq. (7)).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct KronOp {
+  int kA = 0, kB = 0, n_ops = 0;
+  const T* EA = nullptr;
+  const T* EB = nullptr;
+  const T* Acat = nullptr;  // kA x (n_ops kA), coefficients folded in
+  const T* Bcat = nullptr;  // (n_ops kB) x kB
+  long n() const { return (long)kA * kB; }
+};
+
+template <typename T>
+rmc_status kron_apply(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y, T alpha, T beta, T gamma,
+                      const T* Z, T* Tbuf) {
+  const int kA = H.kA, kB = H.kB, no = H.n_ops;
+  if (no > 0) {
+    GemmShape s1{nv * kA, no * kB, kB, kB, kB, 0, 0, 1};
+    EpiKron1<T> e1{Tbuf, kA, kB, nv};
+    gemm_big<T, false, true>(X, H.Bcat, s1, 1, e1, ctx->stream);
+    CKL();
+  }
+  GemmShape s2{kA, nv * kB, no * kA, (long)no * kA, (long)nv * kB, 0, 0, 1};
+  EpiKron2<T> e2{X, Z, H.EA, H.EB, Y, kA, kB, alpha, beta, gamma};
+  if (no > 0) {
+    gemm_big<T, false, false>(H.Acat, Tbuf, s2, 1, e2, ctx->stream);
+  } else {
+    // no coupling: K = 0, the GEMM loop is empty and only the epilogue runs
+    GemmShape s0{kA, nv * kB, 0, 1, (long)nv * kB, 0, 0, 1};
+    gemm_big<T, false, false>(H.EA, X, s0, 1, e2, ctx->stream);
+  }
+  CKL();
+  return RMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Small symmetric eigensolvers.
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO>
+rmc_status jacobi(rmc_ctx* ctx, const TI* S, int m, TO* w, TO* V) {
+  if (m > kMaxSmallDim) return fail(ctx, RMC_ERR_INVAL, "small eigensolver: m=%d exceeds %d", m, kMaxSmallDim);
+  const size_t sm = jacobi_smem_bytes(m);
+  CK(cudaFuncSetAttribute(jacobi_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  jacobi_kernel<TI, TO><<<1, 512, sm, ctx->stream>>>(S, m, w, V, ctx->d_status + 1, 30);
+  CKL();
+  return RMC_OK;
+}
+
+// FP64-accurate: FP32 Jacobi, then Ogita-Aishima refinement steps (at most
+// kOASteps; each step is quadratically convergent, and once a correction is at
+// the FP64 rounding level a device flag makes the remaining launches return
+// at once).
+constexpr int kOASteps = 8;
+
+template <bool TA, bool TB>
+rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, double* C, double beta,
+                         const double* Src, const int* skip) {
+  GemmShape s{m, m, m, m, m, 0, 0, 1};
+  s.skip = skip;
+  EpiAxpby<double> epi{C, Src, m, m, 0, 0, 1.0, beta};
+  gemm_small<double, TA, TB>(A, B, s, 1, epi, ctx->stream);
+  CKL();
+  return RMC_OK;
+}
+
+rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w, double* V) {
+  double *V0, *V1, *R, *AV, *Sp, *lam;
+  int* done;
+  TRY(ws.get(&V0, (size_t)m * m));
+  TRY(ws.get(&V1, (size_t)m * m));
+  TRY(ws.get(&R, (size_t)m * m));
+  TRY(ws.get(&AV, (size_t)m * m));
+  TRY(ws.get(&Sp, (size_t)m * m));
+  TRY(ws.get(&lam, (size_t)m));
+  TRY(ws.get(&done, 1));
+  CK(cudaMemsetAsync(done, 0, sizeof(int), ctx->stream));
+  TRY((jacobi<double, double>(ctx, S, m, lam, V0)));
+  for (int it = 0; it < kOASteps; ++it) {
+    TRY((small_mm_skip<true, false>(ctx, V0, V0, m, R, 0.0, nullptr, done)));
+    identity_minus_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(R, m, done);
+    CKL();
+    TRY((small_mm_skip<false, false>(ctx, S, V0, m, AV, 0.0, nullptr, done)));
+    TRY((small_mm_skip<true, false>(ctx, V0, AV, m, Sp, 0.0, nullptr, done)));
+    oa_correction_kernel<<<1, 512, sizeof(double) * m, ctx->stream>>>(R, Sp, S, m, lam, done);
+    CKL();
+    TRY((small_mm_skip<false, false>(ctx, V0, R, m, V1, 1.0, V0, done)));
+    copy_unless_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(V1, V0, m * m, done);
+    CKL();
+  }
+  sort_pairs_kernel<<<1, 256, 0, ctx->stream>>>(lam, V0, m, w, V);
+  CKL();
+  return RMC_OK;
+}
+
+// Cholesky-QR of a vector-major block in place: two passes, the first with a
+// relative diagonal shift (robust for ill-conditioned filter output).
+template <typename T>
+rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, double shift) {
+  T *G, *Li;
+  TRY(ws.get(&G, (size_t)nv * nv));
+  TRY(ws.get(&Li, (size_t)nv * nv));
+  for (int pass = 0; pass < 2; ++pass) {
+    TRY(gram<T>(ctx, ws, X, nv, X, nv, n, G, true));
+    const size_t sm = cholinv_smem_bytes(nv, sizeof(T));
+    CK(cudaFuncSetAttribute(cholinv_kernel<T, T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    cholinv_kernel<T, T, T><<<1, 512, sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2);
+    CKL();
+    TRY(combine<T>(ctx, Li, false, nv, nv, X, n, tmp, T(1), T(0), nullptr));
+    CK(cudaMemcpyAsync(X, tmp, sizeof(T) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return RMC_OK;
+}
+
+// FP64 Cholesky-QR for a nearly orthonormal block: FP32 Cholesky of the FP64
+// Gram matrix, then two first-order FP64 passes (X <- X - F^T X).
+rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long n, double* tmp) {
+  double *G, *Li;
+  TRY(ws.get(&G, (size_t)nv * nv));
+  TRY(ws.get(&Li, (size_t)nv * nv));
+  TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
+  const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
+  CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  cholinv_kernel<float, double, double><<<1, 512, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
+  CKL();
+  TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
+  CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int pass = 0; pass < 2; ++pass) {
+    TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
+    cholqr_first_order_kernel<<<grid1d((long)nv * nv), 256, 0, ctx->stream>>>(G, nv, Li);
+    CKL();
+    TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, -1.0, 1.0, X));
+    CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return RMC_OK;
+}
+
+rmc_status read_status(rmc_ctx* ctx, int* vals, int count) {
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(vals, ctx->h_pinned, sizeof(int) * count);
+  return RMC_OK;
+}
+
+template <typename T>
+rmc_status to_host(rmc_ctx* ctx, const T* d, double* h, int count) {
+  if (count <= 0) return RMC_OK;
+  if (sizeof(T) * count > kPinnedDoubles * sizeof(double)) return fail(ctx, RMC_ERR_INVAL, "staging too small");
+  CK(cudaMemcpyAsync(ctx->h_pinned, d, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const T* src = (const T*)ctx->h_pinned;
+  for (int i = 0; i < count; ++i) h[i] = (double)src[i];
+  return RMC_OK;
+}
+
+int cut_rule(const std::vector<double>& th, int k_ret, double tau) {
+  const int n = (int)th.size();
+  if (k_ret >= n) return n;
+  for (int kp = k_ret; kp > 0; --kp)
+    if (th[kp] - th[kp - 1] > tau * std::max(1.0, std::fabs(th[kp]))) return kp;
+  return k_ret;
+}
+
+// ---------------------------------------------------------------------------
+// Block construction helpers.
+// ---------------------------------------------------------------------------
+rmc_status new_block(rmc_ctx* ctx, int k, int n_ops, int rows, rmc_block** out) {
+  std::unique_ptr<rmc_block> b(new rmc_block);
+  b->k = k;
+  b->n_ops = n_ops;
+  b->rows = rows;
+  void* p = nullptr;
+  TRY(dalloc(ctx, &p, sizeof(double) * k));
+  b->E = (double*)p;
+  if (n_ops > 0) {
+    rmc_status st = dalloc(ctx, &p, sizeof(double) * (size_t)n_ops * k * k);
+    if (st != RMC_OK) { dfree(ctx, b->E); return st; }
+    b->ops = (double*)p;
+  }
+  if (rows > 0) {
+    rmc_status st = dalloc(ctx, &p, sizeof(double) * (size_t)rows * k);
+    if (st != RMC_OK) { dfree(ctx, b->E); dfree(ctx, b->ops); return st; }
+    b->basis = (double*)p;
+  }
+  b->tags.resize(n_ops);
+  b->opnorm.assign(n_ops, 1.0);
+  *out = b.release();
+  ctx->blocks.insert(*out);
+  return RMC_OK;
+}
+
+void free_block(rmc_ctx* ctx, rmc_block* b) {
+  dfree(ctx, b->E);
+  dfree(ctx, b->ops);
+  dfree(ctx, b->basis);
+  ctx->blocks.erase(b);
+  delete b;
+}
+
+// Leaf from a dense device H (D x D) and dense device operators.
+rmc_status leaf_from_device(rmc_ctx* ctx, Workspace& ws, const double* dH, int D, int k, bool cut,
+                            const std::vector<const double*>& dops, const std::vector<rmc_op_tag>& tags,
+                            const std::vector<double>& norms, rmc_block** out) {
+  if (D > kMaxSmallDim) return fail(ctx, RMC_ERR_INVAL, "leaf dimension %d exceeds %d", D, kMaxSmallDim);
+  double *w, *V;
+  TRY(ws.get(&w, D));
+  TRY(ws.get(&V, (size_t)D * D));
+  TRY(syev64(ctx, ws, dH, D, w, V));
+  std::vector<double> hw(D);
+  TRY(to_host(ctx, w, hw.data(), D));
+  const int kr = std::min(k, D);
+  const int keff = cut ? cut_rule(hw, kr, ctx->cfg.tau_deg) : kr;
+  const int n_ops = (int)dops.size();
+  rmc_block* b = nullptr;
+  TRY(new_block(ctx, keff, n_ops, D, &b));
+  CK(cudaMemcpyAsync(b->E, w, sizeof(double) * keff, cudaMemcpyDeviceToDevice, ctx->stream));
+  // basis[i][r] = V[r][i]: vector-major copy of the first keff columns
+  columns_to_vectors_kernel<double><<<grid1d((long)keff * D), 256, 0, ctx->stream>>>(V, D, keff, b->basis);
+  CKL();
+  gauge_kernel<<<keff, 128, 0, ctx->stream>>>(b->basis, D);
+  CKL();
+  double* Tm;
+  TRY(ws.get(&Tm, (size_t)keff * D));
+  for (int j = 0; j < n_ops; ++j) {
+    // T = U^T O (keff x D), o = T U (keff x keff)
+    GemmShape s1{keff, D, D, D, D, 0, 0, 1};
+    EpiStore<double> e1{Tm, D, 0, 0, 1.0, 0.0};
+    gemm_small<double, false, false>(b->basis, dops[j], s1, 1, e1, ctx->stream);
+    CKL();
+    GemmShape s2{keff, keff, D, D, D, 0, 0, 1};
+    EpiStore<double> e2{b->ops + (size_t)j * keff * keff, keff, 0, 0, 1.0, 0.0};
+    gemm_small<double, false, true>(Tm, b->basis, s2, 1, e2, ctx->stream);
+    CKL();
+    b->tags[j] = tags[j];
+    b->opnorm[j] = norms[j];
+  }
+  *out = b;
+  return RMC_OK;
+}
+
+double host_opnorm2(const double* O, int k) {
+  // power iteration on O^T O for an upper bound of ||O||_2 (k <= 256), then a
+  // 1% margin; exact enough for the filter's spectral bound.
+  std::vector<double> x(k, 1.0 / std::sqrt((double)k)), y(k), z(k);
+  double lam = 0;
+  for (int it = 0; it < 60; ++it) {
+    for (int i = 0; i < k; ++i) { double s = 0; for (int j = 0; j < k; ++j) s += O[i * k + j] * x[j]; y[i] = s; }
+    for (int i = 0; i < k; ++i) { double s = 0; for (int j = 0; j < k; ++j) s += O[j * k + i] * y[j]; z[i] = s; }
+    double nz = 0;
+    for (double v : z) nz += v * v;
+    nz = std::sqrt(nz);
+    if (nz == 0) return 0;
+    lam = nz;
+    for (int i = 0; i < k; ++i) x[i] = z[i] / nz;
+  }
+  double fro = 0;
+  for (int i = 0; i < k * k; ++i) fro += O[i] * O[i];
+  return std::min(std::sqrt(fro), 1.01 * std::sqrt(lam) + 1e-12);
+}
+
+// ---------------------------------------------------------------------------
+// One merge.
+// ---------------------------------------------------------------------------
+struct MergeInput {
+  const rmc_block* A;
+  const rmc_block* B;
+  std::vector<rmc_term> terms;
+  int k_keep;
+  std::vector<rmc_carry> carry;
+  bool top;
+};
+
+template <typename W>
+rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_conv, const int* d_idx,
+                 double ub, double tol, int max_iter, W* X, W* HX, W* theta, int* iters_out, bool* converged) {
+  const long n = H.n();
+  W *Y0, *Y1, *Y2, *Tbuf, *G, *Z, *tmp;
+  double* rn;
+  TRY(ws.get(&Y0, (size_t)b * n));
+  TRY(ws.get(&Y1, (size_t)b * n));
+  TRY(ws.get(&Y2, (size_t)b * n));
+  TRY(ws.get(&tmp, (size_t)b * n));
+  TRY(ws.get(&Tbuf, (size_t)std::max(1, H.n_ops) * b * n));
+  TRY(ws.get(&G, (size_t)b * b));
+  TRY(ws.get(&Z, (size_t)b * b));
+  TRY(ws.get(&rn, (size_t)b));
+  const bool fp64 = sizeof(W) == 8;
+  const double rho = fp64 ? 1e6 : 1e3;  // cap on the filter's amplification ratio
+  const int dmax = 40;
+
+  CK(cudaMemsetAsync(X, 0, sizeof(W) * b * n, ctx->stream));
+  unit_vectors_kernel<W><<<ceil_div(b, 128), 128, 0, ctx->stream>>>(d_idx, b, n, X);
+  CKL();
+  auto rayleigh_ritz = [&]() -> rmc_status {
+    Workspace wl(ctx);
+    TRY(kron_apply<W>(ctx, H, X, b, HX, W(1), W(0), W(0), nullptr, Tbuf));
+    TRY(gram<W>(ctx, wl, X, b, HX, b, n, G, true));
+    if (fp64) {
+      double* w64 = (double*)(void*)theta;
+      TRY(syev64(ctx, wl, (const double*)(const void*)G, b, w64, (double*)(void*)Z));
+    } else {
+      TRY((jacobi<W, W>(ctx, G, b, theta, Z)));
+    }
+    TRY(combine<W>(ctx, Z, true, b, b, X, n, tmp, W(1), W(0), nullptr));
+    std::swap(X, tmp);
+    TRY(combine<W>(ctx, Z, true, b, b, HX, n, tmp, W(1), W(0), nullptr));
+    std::swap(HX, tmp);
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    residual_kernel<W><<<b, 256, 0, ctx->stream>>>(X, HX, theta, n, k_conv, tol, rn, ctx->d_status);
+    CKL();
+    return RMC_OK;
+  };
+  W* X_orig = X;
+  W* HX_orig = HX;
+  TRY(rayleigh_ritz());
+  std::vector<double> th(b);
+  int it = 0;
+  *converged = false;
+  for (;; ++it) {
+    int fails = 0;
+    TRY(read_status(ctx, &fails, 1));
+    TRY(to_host<W>(ctx, theta, th.data(), b));
+    if (fails == 0) { *converged = true; break; }
+    if (it >= max_iter) break;
+    ctx->iterations++;
+    const double a = th[b - 1];
+    const double e = (ub - a) / 2, c = (ub + a) / 2;
+    if (!(e > 0)) break;
+    const double x0 = std::fabs((th[0] - c) / e);
+    int deg = (int)std::floor(std::acosh(rho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+    deg = std::max(2, std::min(dmax, deg));
+    double sigma = e / (th[0] - c);
+    const double tau = 2.0 / sigma;
+    // Y1 = (sigma/e) (H X - c X), from the stored H X
+    axpby_kernel<W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(HX, X, (long)b * n, W(sigma / e),
+                                                                   W(-c * sigma / e), Y1);
+    CKL();
+    W* Yprev = X;  // Y_0 = X
+    W* Ycur = Y1;
+    W* Ynext = Y2;
+    W* spare = Y0;
+    for (int d = 2; d <= deg; ++d) {
+      const double s1 = 1.0 / (tau - sigma);
+      TRY(kron_apply<W>(ctx, H, Ycur, b, Ynext, W(2 * s1 / e), W(-2 * s1 * c / e), W(-sigma * s1), Yprev, Tbuf));
+      // rotate: Yprev <- Ycur, Ycur <- Ynext; Ynext gets the old Yprev buffer
+      // unless that is X (kept intact until the filter ends).
+      W* old_prev = Yprev;
+      Yprev = Ycur;
+      Ycur = Ynext;
+      Ynext = (old_prev == X) ? spare : old_prev;
+      sigma = s1;
+    }
+    // X <- normalised, orthonormalised filter output
+    CK(cudaMemcpyAsync(X, Ycur, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    normalize_kernel<W><<<b, 256, 0, ctx->stream>>>(X, n, nullptr);
+    CKL();
+    {
+      Workspace wl(ctx);
+      TRY(cholqr<W>(ctx, wl, X, b, n, tmp, fp64 ? 1e-14 : 1e-6));
+    }
+    TRY(rayleigh_ritz());
+  }
+  // results must end up in the caller's buffers
+  if (X != X_orig) CK(cudaMemcpyAsync(X_orig, X, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (HX != HX_orig) CK(cudaMemcpyAsync(HX_orig, HX, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  *iters_out = it;
+  return RMC_OK;
+}
+
+template <typename W>
+rmc_status prepare_kron(rmc_ctx* ctx, Workspace& ws, const MergeInput& in, KronOp<W>* H) {
+  const rmc_block* A = in.A;
+  const rmc_block* B = in.B;
+  const int kA = A->k, kB = B->k, no = (int)in.terms.size();
+  H->kA = kA;
+  H->kB = kB;
+  H->n_ops = no;
+  W *EA, *EB, *Araw, *Acat, *Bcat;
+  TRY(ws.get(&EA, kA));
+  TRY(ws.get(&EB, kB));
+  TRY(ws.get(&Araw, (size_t)std::max(1, no) * kA * kA));
+  TRY(ws.get(&Acat, (size_t)std::max(1, no) * kA * kA));
+  TRY(ws.get(&Bcat, (size_t)std::max(1, no) * kB * kB));
+  convert_kernel<W, double><<<grid1d(kA), 256, 0, ctx->stream>>>(A->E, EA, kA);
+  CKL();
+  convert_kernel<W, double><<<grid1d(kB), 256, 0, ctx->stream>>>(B->E, EB, kB);
+  CKL();
+  Coefs cf{};
+  for (int j = 0; j < no; ++j) {
+    const rmc_term& t = in.terms[j];
+    cf.c[j] = t.coef;
+    convert_kernel<W, double><<<grid1d((long)kA * kA), 256, 0, ctx->stream>>>(
+        A->ops + (size_t)t.op_a * kA * kA, Araw + (size_t)j * kA * kA, (long)kA * kA);
+    CKL();
+    convert_kernel<W, double><<<grid1d((long)kB * kB), 256, 0, ctx->stream>>>(
+        B->ops + (size_t)t.op_b * kB * kB, Bcat + (size_t)j * kB * kB, (long)kB * kB);
+    CKL();
+  }
+  if (no > 0) {
+    build_acat_kernel<W><<<grid1d((long)kA * kA * no), 256, 0, ctx->stream>>>(Araw, cf, kA, no, Acat);
+    CKL();
+  }
+  H->EA = EA;
+  H->EB = EB;
+  H->Acat = Acat;
+  H->Bcat = Bcat;
+  return RMC_OK;
+}
+
+template <typename W>
+rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_status* soft) {
+  Workspace ws(ctx);
+  const rmc_block* A = in.A;
+  const rmc_block* B = in.B;
+  const int kA = A->k, kB = B->k, no = (int)in.terms.size();
+  const long n = (long)kA * kB;
+  const int k_ret = (int)std::min<long>(in.k_keep, n);
+  int g = ctx->cfg.guard > 0 ? ctx->cfg.guard : std::max(16, k_ret / 2);
+  int b = (int)std::min<long>(n, (long)k_ret + g);
+  b = std::min(b, kMaxSmallDim);
+  if (b < k_ret) return fail(ctx, RMC_ERR_INVAL, "kept count %d exceeds the solver block limit %d", k_ret, kMaxSmallDim);
+  const int k_conv = std::min(b, in.top ? k_ret : k_ret + 1);
+
+  // FP64 operator copies for the diagonal, the finalisation and the rotation
+  KronOp<double> H64;
+  TRY(prepare_kron<double>(ctx, ws, in, &H64));
+  double* D;
+  int* idx;
+  double* dmm;
+  TRY(ws.get(&D, n));
+  TRY(ws.get(&idx, b));
+  TRY(ws.get(&dmm, 2));
+  {
+    Coefs cf{};
+    double *Ad, *Bd;
+    TRY(ws.get(&Ad, (size_t)std::max(1, no) * kA * kA));
+    TRY(ws.get(&Bd, (size_t)std::max(1, no) * kB * kB));
+    for (int j = 0; j < no; ++j) {
+      cf.c[j] = in.terms[j].coef;
+      CK(cudaMemcpyAsync(Ad + (size_t)j * kA * kA, A->ops + (size_t)in.terms[j].op_a * kA * kA,
+                         sizeof(double) * kA * kA, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(Bd + (size_t)j * kB * kB, B->ops + (size_t)in.terms[j].op_b * kB * kB,
+                         sizeof(double) * kB * kB, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    diag_kernel<<<grid1d(n), 256, 0, ctx->stream>>>(A->E, B->E, Ad, Bd, cf, no, kA, kB, D);
+    CKL();
+    select_smallest_kernel<<<1, 1024, 0, ctx->stream>>>(D, n, b, idx, dmm);
+    CKL();
+  }
+  double hdmm[2];
+  TRY(to_host<double>(ctx, dmm, hdmm, 2));
+  double ub = hdmm[1];
+  for (int j = 0; j < no; ++j) {
+    const rmc_term& t = in.terms[j];
+    ub += std::fabs(t.coef) * A->opnorm[t.op_a] * B->opnorm[t.op_b];
+  }
+  ub += 1e-12 * std::max(1.0, std::fabs(ub));
+
+  double *X64, *HX64, *tmp64, *Tb64;
+  TRY(ws.get(&X64, (size_t)b * n));
+  TRY(ws.get(&HX64, (size_t)b * n));
+  TRY(ws.get(&tmp64, (size_t)b * n));
+  TRY(ws.get(&Tb64, (size_t)std::max(1, no) * b * n));
+  bool converged = true;
+  int iters = 0;
+  const bool dense = (b == n);
+  if (dense) {
+    CK(cudaMemsetAsync(X64, 0, sizeof(double) * b * n, ctx->stream));
+    unit_vectors_kernel<double><<<ceil_div(b, 128), 128, 0, ctx->stream>>>(idx, b, n, X64);
+    CKL();
+  } else {
+    const double tol = ctx->cfg.tol;
+    if (sizeof(W) == 8) {
+      double* th;
+      TRY(ws.get(&th, b));
+      TRY((chfsi<double>(ctx, ws, H64, b, k_conv, idx, ub, tol, ctx->cfg.max_iter, X64, HX64, th, &iters, &converged)));
+    } else {
+      KronOp<W> Hw;
+      TRY(prepare_kron<W>(ctx, ws, in, &Hw));
+      W *Xw, *HXw, *thw;
+      TRY(ws.get(&Xw, (size_t)b * n));
+      TRY(ws.get(&HXw, (size_t)b * n));
+      TRY(ws.get(&thw, b));
+      const double tolw = ctx->cfg.precision == RMC_PREC_FP64 ? tol : std::max(tol, 2e-6);
+      TRY((chfsi<W>(ctx, ws, Hw, b, k_conv, idx, ub, tolw, ctx->cfg.max_iter, Xw, HXw, thw, &iters, &converged)));
+      convert_kernel<double, W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(Xw, X64, (long)b * n);
+      CKL();
+    }
+  }
+  // FP64 finalisation: orthonormalise, project, refined small eigensolve, rotate.
+  TRY(cholqr64_refine(ctx, ws, X64, b, n, tmp64));
+  TRY(kron_apply<double>(ctx, H64, X64, b, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+  double *Gs, *w, *Zs;
+  TRY(ws.get(&Gs, (size_t)b * b));
+  TRY(ws.get(&w, b));
+  TRY(ws.get(&Zs, (size_t)b * b));
+  TRY(gram<double>(ctx, ws, X64, b, HX64, b, n, Gs, true));
+  TRY(syev64(ctx, ws, Gs, b, w, Zs));
+  double* C = tmp64;
+  TRY(combine<double>(ctx, Zs, true, b, b, X64, n, C, 1.0, 0.0, nullptr));
+  std::vector<double> th(b);
+  TRY(to_host<double>(ctx, w, th.data(), b));
+  int keff = k_ret;
+  if (!in.top && k_ret < n) {
+    std::vector<double> tfull(th.begin(), th.begin() + std::min<long>(b, n));
+    keff = cut_rule(tfull, k_ret, ctx->cfg.tau_deg);
+  }
+  gauge_kernel<<<keff, 256, 0, ctx->stream>>>(C, n);
+  CKL();
+  const int nc = (int)in.carry.size();
+  rmc_block* blk = nullptr;
+  TRY(new_block(ctx, keff, nc, (int)n, &blk));
+  CK(cudaMemcpyAsync(blk->E, w, sizeof(double) * keff, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(blk->basis, C, sizeof(double) * keff * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  // rotate carried operators: out = C^T (o (x) I) C or C^T (I (x) o) C
+  double* Tr = Tb64;
+  for (int j = 0; j < nc; ++j) {
+    const rmc_carry& cr = in.carry[j];
+    const rmc_block* src = cr.side == 0 ? A : B;
+    const double* o = src->ops + (size_t)cr.op * src->k * src->k;
+    if (cr.side == 0) {
+      GemmShape s{kA, kB, kA, kA, kB, 0, n, 1};
+      EpiAxpby<double> e{Tr, nullptr, kB, 0, n, 0, 1.0, 0.0};
+      gemm_big<double, false, false>(o, blk->basis, s, keff, e, ctx->stream);
+    } else {
+      GemmShape s{keff * kA, kB, kB, kB, kB, 0, 0, 1};
+      EpiAxpby<double> e{Tr, nullptr, kB, 0, 0, 0, 1.0, 0.0};
+      gemm_big<double, false, true>(blk->basis, o, s, 1, e, ctx->stream);
+    }
+    CKL();
+    TRY(gram<double>(ctx, ws, blk->basis, keff, Tr, keff, n, blk->ops + (size_t)j * keff * keff, false));
+    blk->tags[j] = src->tags[cr.op];
+    blk->opnorm[j] = src->opnorm[cr.op];
+  }
+  int st[3];
+  TRY(read_status(ctx, st, 3));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 3, ctx->stream));
+  *out = blk;
+  *soft = converged ? RMC_OK : RMC_ERR_NOCONV;
+  if (!converged) fail(ctx, RMC_ERR_NOCONV, "subspace iteration did not converge in %d iterations (n=%ld)", iters, n);
+  return RMC_OK;
+}
+
+rmc_status check_ctx(rmc_ctx* ctx) {
+  if (!ctx) return RMC_ERR_INVAL;
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  return RMC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+rmc_status rmc_create(rmc_ctx** out, const rmc_config* cfg_in) {
+  if (!out) return RMC_ERR_INVAL;
+  *out = nullptr;
+  rmc_config cfg{};
+  if (cfg_in) cfg = *cfg_in;
+  std::unique_ptr<rmc_ctx> c(new rmc_ctx);
+  rmc_ctx* ctx = c.get();
+  if (cfg.mem_budget == 0) cfg.mem_budget = (size_t)40 << 30;
+  if (cfg.precision < 0 || cfg.precision > 2) return RMC_ERR_INVAL;
+  if (cfg.tol <= 0) cfg.tol = cfg.precision == RMC_PREC_FP64 ? 1e-11 : 2e-6;
+  if (cfg.max_iter <= 0) cfg.max_iter = 200;
+  if (cfg.tau_deg <= 0) cfg.tau_deg = 1e-7;
+  ctx->cfg = cfg;
+  ctx->device = cfg.device;
+  ctx->budget = cfg.mem_budget;
+  CK(cudaSetDevice(ctx->device));
+  if (cfg.stream) {
+    ctx->stream = (cudaStream_t)cfg.stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = ctx->device;
+  CK(cudaMemPoolCreate(&ctx->pool, &props));
+  uint64_t thr = UINT64_MAX;
+  CK(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  CK(cudaMalloc(&ctx->d_status, 64 * sizeof(int)));
+  CK(cudaMemset(ctx->d_status, 0, 64 * sizeof(int)));
+  CK(cudaMallocHost(&ctx->h_pinned, kPinnedDoubles * sizeof(double)));
+  *out = c.release();
+  return RMC_OK;
+}
+
+rmc_status rmc_destroy(rmc_ctx* ctx) {
+  if (!ctx) return RMC_ERR_INVAL;
+  cudaSetDevice(ctx->device);
+  std::vector<rmc_block*> bl(ctx->blocks.begin(), ctx->blocks.end());
+  for (rmc_block* b : bl) free_block(ctx, b);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return RMC_OK;
+}
+
+const char* rmc_last_error(const rmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+size_t rmc_mem_in_use(const rmc_ctx* ctx) { return ctx ? ctx->in_use : 0; }
+void* rmc_stream(const rmc_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+rmc_status rmc_stats(const rmc_ctx* ctx, uint64_t* launches, uint64_t* iterations) {
+  if (!ctx) return RMC_ERR_INVAL;
+  if (launches) *launches = ctx->launches;
+  if (iterations) *iterations = ctx->iterations;
+  return RMC_OK;
+}
+
+rmc_status rmc_build_leaf(rmc_ctx* ctx, const double* H, int D, int k, const double* const* ops,
+                          const rmc_op_tag* tags, int n_ops, rmc_block** out) {
+  TRY(check_ctx(ctx));
+  if (!H || !out || D < 1 || D > kMaxSmallDim || k < 1 || n_ops < 0 || n_ops > 4 * kMaxOps || (n_ops && !ops))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf: bad arguments (D=%d k=%d n_ops=%d)", D, k, n_ops);
+  double hmax = 0;
+  for (int i = 0; i < D * D; ++i) {
+    if (!std::isfinite(H[i])) return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf: H has a non-finite entry");
+    hmax = std::max(hmax, std::fabs(H[i]));
+  }
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(H[i * D + j] - H[j * D + i]) > 1e-12 * std::max(1.0, hmax))
+        return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf: H is not symmetric at (%d,%d)", i, j);
+  Workspace ws(ctx);
+  double* dH;
+  TRY(ws.get(&dH, (size_t)D * D));
+  CK(cudaMemcpyAsync(dH, H, sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<const double*> dops(n_ops);
+  std::vector<rmc_op_tag> tg(n_ops);
+  std::vector<double> nrm(n_ops);
+  for (int j = 0; j < n_ops; ++j) {
+    if (!ops[j]) return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf: operator %d is NULL", j);
+    for (int i = 0; i < D * D; ++i)
+      if (!std::isfinite(ops[j][i])) return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf: operator %d non-finite", j);
+    double* d;
+    TRY(ws.get(&d, (size_t)D * D));
+    CK(cudaMemcpyAsync(d, ops[j], sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
+    dops[j] = d;
+    tg[j] = tags ? tags[j] : rmc_op_tag{-1, 'O'};
+    nrm[j] = host_opnorm2(ops[j], D);
+  }
+  TRY(leaf_from_device(ctx, ws, dH, D, k, true, dops, tg, nrm, out));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RMC_OK;
+}
+
+static int pauli_code(char p) {
+  switch (p) {
+    case 'X': case 'x': return 1;
+    case 'Y': case 'y': return 2;
+    case 'Z': case 'z': return 3;
+    default: return 0;
+  }
+}
+
+rmc_status rmc_build_leaf_pauli(rmc_ctx* ctx, int L, int k, int n_onsite, const int* onsite_site,
+                                const char* onsite_pauli, const double* onsite_coef, int n_bonds, const int* bond_i,
+                                const int* bond_j, const char* bond_pauli_i, const char* bond_pauli_j,
+                                const double* bond_coef, int n_carry, const rmc_op_tag* carry, rmc_block** out) {
+  TRY(check_ctx(ctx));
+  if (L < 1 || (1 << L) > kMaxSmallDim || k < 1 || n_onsite < 0 || n_bonds < 0 || n_carry < 0 || !out ||
+      n_carry > 4 * kMaxOps)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf_pauli: bad sizes (L=%d k=%d)", L, k);
+  std::vector<PauliTerm> terms;
+  for (int t = 0; t < n_onsite; ++t) {
+    const int c = pauli_code(onsite_pauli[t]);
+    if (c == 0 || c == 2 || onsite_site[t] < 0 || onsite_site[t] >= L || !std::isfinite(onsite_coef[t]))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf_pauli: bad on-site term %d (a Y field is imaginary)", t);
+    terms.push_back(PauliTerm{onsite_site[t], -1, c, 0, onsite_coef[t]});
+  }
+  for (int t = 0; t < n_bonds; ++t) {
+    const int ci = pauli_code(bond_pauli_i[t]), cj = pauli_code(bond_pauli_j[t]);
+    if (!ci || !cj || (ci == 2) != (cj == 2) || bond_i[t] < 0 || bond_j[t] >= L || bond_i[t] >= bond_j[t] ||
+        !std::isfinite(bond_coef[t]))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf_pauli: bad bond %d", t);
+    // Y Y = -(iY)(iY): the real representation carries iY
+    const double cf = (ci == 2) ? -bond_coef[t] : bond_coef[t];
+    terms.push_back(PauliTerm{bond_i[t], bond_j[t], ci, cj, cf});
+  }
+  const int D = 1 << L;
+  Workspace ws(ctx);
+  PauliTerm* dterms;
+  TRY(ws.get(&dterms, std::max<size_t>(1, terms.size())));
+  if (!terms.empty())
+    CK(cudaMemcpyAsync(dterms, terms.data(), sizeof(PauliTerm) * terms.size(), cudaMemcpyHostToDevice, ctx->stream));
+  double* dH;
+  TRY(ws.get(&dH, (size_t)D * D));
+  pauli_matrix_kernel<<<1, 256, 0, ctx->stream>>>(dterms, (int)terms.size(), L, dH);
+  CKL();
+  std::vector<const double*> dops(n_carry);
+  std::vector<rmc_op_tag> tg(n_carry);
+  std::vector<double> nrm(n_carry, 1.0);
+  PauliTerm* dct;
+  TRY(ws.get(&dct, std::max(1, n_carry)));
+  std::vector<PauliTerm> ct(n_carry);
+  for (int j = 0; j < n_carry; ++j) {
+    const int c = pauli_code(carry[j].pauli);
+    if (!c || carry[j].site < 0 || carry[j].site >= L)
+      return fail(ctx, RMC_ERR_INVAL, "rmc_build_leaf_pauli: bad carried operator %d", j);
+    ct[j] = PauliTerm{carry[j].site, -1, c, 0, 1.0};
+    tg[j] = carry[j];
+  }
+  if (n_carry) CK(cudaMemcpyAsync(dct, ct.data(), sizeof(PauliTerm) * n_carry, cudaMemcpyHostToDevice, ctx->stream));
+  for (int j = 0; j < n_carry; ++j) {
+    double* d;
+    TRY(ws.get(&d, (size_t)D * D));
+    pauli_matrix_kernel<<<1, 256, 0, ctx->stream>>>(dct + j, 1, L, d);
+    CKL();
+    dops[j] = d;
+  }
+  TRY(leaf_from_device(ctx, ws, dH, D, k, true, dops, tg, nrm, out));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RMC_OK;
+}
+
+rmc_status rmc_couple(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B, const rmc_term* terms, int n_terms,
+                      int k_keep, const rmc_carry* carry, int n_carry, int flags, rmc_block** out) {
+  TRY(check_ctx(ctx));
+  if (!A || !B || !out || k_keep < 1 || n_terms < 0 || n_terms > kMaxOps || n_carry < 0 || n_carry > 4 * kMaxOps ||
+      (n_terms && !terms) || (n_carry && !carry))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_couple: bad arguments");
+  MergeInput in;
+  in.A = A;
+  in.B = B;
+  in.k_keep = k_keep;
+  in.top = (flags & RMC_COUPLE_TOP) != 0;
+  for (int t = 0; t < n_terms; ++t) {
+    if (terms[t].op_a < 0 || terms[t].op_a >= A->n_ops || terms[t].op_b < 0 || terms[t].op_b >= B->n_ops ||
+        !std::isfinite(terms[t].coef))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_couple: term %d refers to a missing operator", t);
+    in.terms.push_back(terms[t]);
+  }
+  for (int c = 0; c < n_carry; ++c) {
+    const rmc_block* s = carry[c].side == 0 ? A : (carry[c].side == 1 ? B : nullptr);
+    if (!s || carry[c].op < 0 || carry[c].op >= s->n_ops)
+      return fail(ctx, RMC_ERR_INVAL, "rmc_couple: carry %d refers to a missing operator", c);
+    in.carry.push_back(carry[c]);
+  }
+  rmc_status soft = RMC_OK;
+  rmc_status st = (ctx->cfg.precision == RMC_PREC_FP64) ? couple_impl<double>(ctx, in, out, &soft)
+                                                        : couple_impl<float>(ctx, in, out, &soft);
+  if (st != RMC_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, RMC_ERR_CUDA, "rmc_couple: %s", cudaGetErrorString(e));
+  return soft;
+}
+
+rmc_status rmc_lowest(rmc_ctx* ctx, const rmc_block* blk, int q, double* E_out, double* C_out, int* k_eff_out) {
+  TRY(check_ctx(ctx));
+  if (!blk || !E_out || q < 1) return fail(ctx, RMC_ERR_INVAL, "rmc_lowest: bad arguments");
+  const int qq = std::min(q, blk->k);
+  CK(cudaMemcpyAsync(E_out, blk->E, sizeof(double) * qq, cudaMemcpyDeviceToHost, ctx->stream));
+  if (C_out && blk->rows > 0) {
+    std::vector<double> tmp((size_t)qq * blk->rows);
+    CK(cudaMemcpyAsync(tmp.data(), blk->basis, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < qq; ++i)
+      for (int r = 0; r < blk->rows; ++r) C_out[(size_t)r * qq + i] = tmp[(size_t)i * blk->rows + r];
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (k_eff_out) *k_eff_out = qq;
+  return RMC_OK;
+}
+
+rmc_status rmc_block_free(rmc_ctx* ctx, rmc_block* blk) {
+  if (!ctx || !blk) return RMC_ERR_INVAL;
+  if (!ctx->blocks.count(blk)) return fail(ctx, RMC_ERR_INVAL, "rmc_block_free: unknown block");
+  cudaSetDevice(ctx->device);
+  free_block(ctx, blk);
+  return RMC_OK;
+}
+
+rmc_status rmc_block_info(const rmc_block* blk, int* k, int* n_ops, int* rows, rmc_op_tag* tags) {
+  if (!blk) return RMC_ERR_INVAL;
+  if (k) *k = blk->k;
+  if (n_ops) *n_ops = blk->n_ops;
+  if (rows) *rows = blk->rows;
+  if (tags)
+    for (int j = 0; j < blk->n_ops; ++j) tags[j] = blk->tags[j];
+  return RMC_OK;
+}
+
+rmc_status rmc_block_export(rmc_ctx* ctx, const rmc_block* blk, double* E, double* ops, double* basis) {
+  TRY(check_ctx(ctx));
+  if (!blk) return fail(ctx, RMC_ERR_INVAL, "rmc_block_export: null block");
+  if (E) CK(cudaMemcpyAsync(E, blk->E, sizeof(double) * blk->k, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ops && blk->n_ops)
+    CK(cudaMemcpyAsync(ops, blk->ops, sizeof(double) * blk->n_ops * blk->k * blk->k, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (basis && blk->rows)
+    CK(cudaMemcpyAsync(basis, blk->basis, sizeof(double) * blk->rows * blk->k, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RMC_OK;
+}
+
+rmc_status rmc_block_import(rmc_ctx* ctx, int k, const double* E, int n_ops, const double* ops,
+                            const rmc_op_tag* tags, int rows, const double* basis, rmc_block** out) {
+  TRY(check_ctx(ctx));
+  if (k < 1 || !E || n_ops < 0 || (n_ops && !ops) || rows < 0 || (rows && !basis) || !out)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_block_import: bad arguments");
+  for (int i = 0; i < k; ++i)
+    if (!std::isfinite(E[i]) || (i && E[i] < E[i - 1]))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_block_import: energies must be finite and ascending");
+  rmc_block* b = nullptr;
+  TRY(new_block(ctx, k, n_ops, rows, &b));
+  CK(cudaMemcpyAsync(b->E, E, sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream));
+  if (n_ops) CK(cudaMemcpyAsync(b->ops, ops, sizeof(double) * n_ops * k * k, cudaMemcpyHostToDevice, ctx->stream));
+  if (rows) CK(cudaMemcpyAsync(b->basis, basis, sizeof(double) * rows * k, cudaMemcpyHostToDevice, ctx->stream));
+  for (int j = 0; j < n_ops; ++j) {
+    b->tags[j] = tags ? tags[j] : rmc_op_tag{-1, 'O'};
+    b->opnorm[j] = host_opnorm2(ops + (size_t)j * k * k, k);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = b;
+  return RMC_OK;
+}
+
+rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv, const void* EA,
+                           const void* EB, const void* A, const void* B, const double* coef, const void* X, void* Y,
+                           const void* Z, double alpha, double beta, double gamma) {
+  TRY(check_ctx(ctx));
+  if (kA < 1 || kB < 1 || n_ops < 0 || n_ops > kMaxOps || nv < 1 || !EA || !EB || !X || !Y ||
+      (n_ops && (!A || !B || !coef)) || (gamma != 0.0 && !Z) || (dtype != 0 && dtype != 1) || X == Y || Z == Y)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_kron_matvec: bad arguments");
+  Workspace ws(ctx);
+  Coefs cf{};
+  for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
+  auto run = [&](auto tag) -> rmc_status {
+    using T = decltype(tag);
+    KronOp<T> H;
+    H.kA = kA;
+    H.kB = kB;
+    H.n_ops = n_ops;
+    H.EA = (const T*)EA;
+    H.EB = (const T*)EB;
+    H.Bcat = (const T*)B;
+    T *Acat, *Tbuf;
+    TRY(ws.get(&Acat, (size_t)std::max(1, n_ops) * kA * kA));
+    TRY(ws.get(&Tbuf, (size_t)std::max(1, n_ops) * kA * kB * nv));
+    if (n_ops) {
+      build_acat_kernel<T><<<grid1d((long)kA * kA * n_ops), 256, 0, ctx->stream>>>((const T*)A, cf, kA, n_ops, Acat);
+      CKL();
+    }
+    H.Acat = Acat;
+    return kron_apply<T>(ctx, H, (const T*)X, nv, (T*)Y, (T)alpha, (T)beta, (T)gamma, (const T*)Z, Tbuf);
+  };
+  return dtype == 0 ? run(double{}) : run(float{});
+}
+
+rmc_status rmc_syev(rmc_ctx* ctx, int m, const double* S, double* w, double* V) {
+  TRY(check_ctx(ctx));
+  if (m < 1 || m > kMaxSmallDim || !S || !w || !V) return fail(ctx, RMC_ERR_INVAL, "rmc_syev: bad arguments");
+  Workspace ws(ctx);
+  TRY(syev64(ctx, ws, S, m, w, V));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RMC_OK;
+}
+
+rmc_status rmc_rotate_op(rmc_ctx* ctx, int side, int kA, int kB, int kr, const double* C, const double* o,
+                         double* out) {
+  TRY(check_ctx(ctx));
+  if ((side != 0 && side != 1) || kA < 1 || kB < 1 || kr < 1 || !C || !o || !out)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_rotate_op: bad arguments");
+  Workspace ws(ctx);
+  const long n = (long)kA * kB;
+  double* Tr;
+  TRY(ws.get(&Tr, (size_t)kr * n));
+  if (side == 0) {
+    GemmShape s{kA, kB, kA, kA, kB, 0, n, 1};
+    EpiAxpby<double> e{Tr, nullptr, kB, 0, n, 0, 1.0, 0.0};
+    gemm_big<double, false, false>(o, C, s, kr, e, ctx->stream);
+  } else {
+    GemmShape s{kr * kA, kB, kB, kB, kB, 0, 0, 1};
+    EpiAxpby<double> e{Tr, nullptr, kB, 0, 0, 0, 1.0, 0.0};
+    gemm_big<double, false, true>(C, o, s, 1, e, ctx->stream);
+  }
+  CKL();
+  TRY(gram<double>(ctx, ws, C, kr, Tr, kr, n, out, false));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RMC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Recursion loop of Algorithm 1 over a chain (host scheduler).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CTerm {  // on-site (j < 0) or two-site term with chain-global sites
+  int i, j;
+  char pi, pj;
+  double coef;
+};
+
+struct ChainNode {
+  int lo, hi;
+  int left = -1, right = -1;
+  std::string sig;
+  std::vector<std::pair<int, char>> carry;  // relative (site, pauli), sorted
+};
+
+int build_tree(std::vector<ChainNode>& nodes, int lo, int hi, int L0) {
+  nodes.push_back(ChainNode{lo, hi});
+  const int id = (int)nodes.size() - 1;
+  if (hi - lo > L0) {
+    const int mid = lo + (hi - lo) / 2;
+    const int l = build_tree(nodes, lo, mid, L0);
+    const int r = build_tree(nodes, mid, hi, L0);
+    nodes[id].left = l;
+    nodes[id].right = r;
+  }
+  return id;
+}
+
+// Signature of a block: its length and every term lying inside it, with
+// sites relative to its first site.  Blocks with equal signatures have equal
+// spectra and operator matrices (the paper's homogeneous reuse).
+std::string signature(const std::vector<CTerm>& terms, int lo, int hi) {
+  std::vector<std::string> parts;
+  char buf[128];
+  for (const CTerm& t : terms) {
+    const bool in = t.j < 0 ? (t.i >= lo && t.i < hi) : (t.i >= lo && t.j < hi);
+    if (!in) continue;
+    snprintf(buf, sizeof buf, "%d,%d,%c,%c,%.17g", t.i - lo, t.j < 0 ? -1 : t.j - lo, t.pi, t.j < 0 ? '-' : t.pj, t.coef);
+    parts.push_back(buf);
+  }
+  std::sort(parts.begin(), parts.end());
+  std::string s = std::to_string(hi - lo) + "|";
+  for (auto& p : parts) s += p + ";";
+  return s;
+}
+
+int find_tag(const rmc_block* b, int site, char p) {
+  for (int j = 0; j < b->n_ops; ++j)
+    if (b->tags[j].site == site && b->tags[j].pauli == p) return j;
+  return -1;
+}
+
+}  // namespace
+
+extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int n_onsite,
+                                      const int* onsite_site, const char* onsite_pauli, const double* onsite_coef,
+                                      int n_bonds, const int* bond_i, const int* bond_j, const char* bond_pauli_i,
+                                      const char* bond_pauli_j, const double* bond_coef, double* E_out) {
+  TRY(check_ctx(ctx));
+  if (n_sites < 1 || L0 < 1 || k < 1 || q < 1 || n_onsite < 0 || n_bonds < 0 || !E_out)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: bad arguments");
+  std::vector<CTerm> terms;
+  for (int t = 0; t < n_onsite; ++t) {
+    if (onsite_site[t] < 0 || onsite_site[t] >= n_sites)
+      return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: on-site term %d out of range", t);
+    terms.push_back(CTerm{onsite_site[t], -1, (char)toupper(onsite_pauli[t]), 0, onsite_coef[t]});
+  }
+  for (int t = 0; t < n_bonds; ++t) {
+    if (bond_i[t] < 0 || bond_j[t] >= n_sites || bond_i[t] >= bond_j[t])
+      return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: bond %d out of range", t);
+    terms.push_back(CTerm{bond_i[t], bond_j[t], (char)toupper(bond_pauli_i[t]), (char)toupper(bond_pauli_j[t]),
+                          bond_coef[t]});
+  }
+  std::vector<ChainNode> nodes;
+  build_tree(nodes, 0, n_sites, L0);
+  // carried operators per node: inside ends of terms crossing its boundary;
+  // nodes with one signature carry the union so one block serves them all.
+  std::map<std::string, std::set<std::pair<int, char>>> need;
+  for (ChainNode& nd : nodes) {
+    nd.sig = signature(terms, nd.lo, nd.hi);
+    auto& st = need[nd.sig];
+    for (const CTerm& t : terms) {
+      if (t.j < 0) continue;
+      const bool iin = t.i >= nd.lo && t.i < nd.hi, jin = t.j >= nd.lo && t.j < nd.hi;
+      if (iin && !jin) st.insert({t.i - nd.lo, t.pi});
+      if (jin && !iin) st.insert({t.j - nd.lo, t.pj});
+    }
+  }
+  for (ChainNode& nd : nodes) nd.carry.assign(need[nd.sig].begin(), need[nd.sig].end());
+
+  std::map<std::string, rmc_block*> cache;
+  std::vector<rmc_block*> owned;
+  rmc_status soft = RMC_OK;
+  auto cleanup = [&]() {
+    for (rmc_block* b : owned) free_block(ctx, b);
+  };
+  std::function<rmc_status(int, bool, rmc_block**)> build = [&](int id, bool top, rmc_block** out) -> rmc_status {
+    const ChainNode& nd = nodes[id];
+    if (!top) {
+      auto it = cache.find(nd.sig);
+      if (it != cache.end()) { *out = it->second; return RMC_OK; }
+    }
+    rmc_block* blk = nullptr;
+    if (nd.left < 0) {
+      const int L = nd.hi - nd.lo;
+      std::vector<int> os, bi, bj;
+      std::vector<char> op, pi, pj;
+      std::vector<double> oc, bc;
+      for (const CTerm& t : terms) {
+        if (t.j < 0 && t.i >= nd.lo && t.i < nd.hi) { os.push_back(t.i - nd.lo); op.push_back(t.pi); oc.push_back(t.coef); }
+        if (t.j >= 0 && t.i >= nd.lo && t.j < nd.hi) {
+          bi.push_back(t.i - nd.lo); bj.push_back(t.j - nd.lo); pi.push_back(t.pi); pj.push_back(t.pj); bc.push_back(t.coef);
+        }
+      }
+      std::vector<rmc_op_tag> cr;
+      for (auto& c : nd.carry) cr.push_back(rmc_op_tag{c.first, c.second});
+      TRY(rmc_build_leaf_pauli(ctx, L, top ? (1 << L) : k, (int)os.size(), os.data(), op.data(), oc.data(),
+                               (int)bi.size(), bi.data(), bj.data(), pi.data(), pj.data(), bc.data(), (int)cr.size(),
+                               cr.data(), &blk));
+    } else {
+      rmc_block *A = nullptr, *B = nullptr;
+      TRY(build(nd.left, false, &A));
+      TRY(build(nd.right, false, &B));
+      const int Alo = nodes[nd.left].lo, Blo = nodes[nd.right].lo, Bhi = nodes[nd.right].hi;
+      std::vector<rmc_term> mt;
+      for (const CTerm& t : terms) {
+        if (t.j < 0 || !(t.i >= Alo && t.i < Blo && t.j >= Blo && t.j < Bhi)) continue;
+        const int oa = find_tag(A, t.i - Alo, t.pi), ob = find_tag(B, t.j - Blo, t.pj);
+        if (oa < 0 || ob < 0) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing carried operator");
+        // Y Y = -(iY)(iY): carried Y operators are iY
+        mt.push_back(rmc_term{(t.pi == 'Y' && t.pj == 'Y') ? -t.coef : t.coef, oa, ob});
+      }
+      std::vector<rmc_carry> cy;
+      if (!top) {
+        for (auto& c : nd.carry) {
+          const int gsite = nd.lo + c.first;
+          if (gsite < Blo) cy.push_back(rmc_carry{0, find_tag(A, gsite - Alo, c.second)});
+          else cy.push_back(rmc_carry{1, find_tag(B, gsite - Blo, c.second)});
+          if (cy.back().op < 0) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing operator to carry");
+        }
+      }
+      rmc_status st = rmc_couple(ctx, A, B, mt.data(), (int)mt.size(), top ? q : k, cy.data(), (int)cy.size(),
+                                 top ? RMC_COUPLE_TOP : 0, &blk);
+      if (st == RMC_ERR_NOCONV) soft = st;
+      else if (st != RMC_OK) return st;
+      // re-base inherited tags to this block's first site
+      for (size_t j = 0; j < cy.size(); ++j) {
+        const ChainNode& src = nodes[cy[j].side == 0 ? nd.left : nd.right];
+        blk->tags[j].site += src.lo - nd.lo;
+      }
+    }
+    owned.push_back(blk);
+    if (!top) cache[nd.sig] = blk;
+    *out = blk;
+    return RMC_OK;
+  };
+  rmc_block* topb = nullptr;
+  rmc_status st = build(0, true, &topb);
+  if (st != RMC_OK) {
+    std::string e = ctx->err;
+    cleanup();
+    ctx->err = e;
+    return st;
+  }
+  std::vector<double> E(std::min(q, topb->k));
+  st = rmc_lowest(ctx, topb, q, E.data(), nullptr, nullptr);
+  for (int i = 0; i < q; ++i) E_out[i] = i < (int)E.size() ? E[i] : NAN;
+  cleanup();
+  if (st != RMC_OK) return st;
+  if (soft != RMC_OK) return fail(ctx, soft, "rmc_solve_chain: a merge did not converge");
+  return RMC_OK;
+}

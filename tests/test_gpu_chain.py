@@ -1,0 +1,69 @@
+"""Whole-chain parity (the recursion loop of Algorithm 1) against the oracle:
+energies within 1e-10 relative (FP64 path) or 1e-8 (mixed path), at the
+workload sizes, plus free-fermion and exact-diagonalisation checks."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import closed_forms as CF
+from oracle import rmc_oracle as O
+from tests.gpu_util import torch_cuda
+
+import paper_2609_02394_b300 as P
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+RTOL = {"fp64": 1e-10, "mixed": 1e-8}
+
+
+@pytest.fixture(scope="module", params=["fp64", "mixed"])
+def ctx(request):
+    torch_cuda()
+    c = P.Context(precision=request.param)
+    yield c
+    c.close()
+
+
+def _close(ctx, got, ref):
+    tol = RTOL[ctx.precision] * np.maximum(1.0, np.abs(ref))
+    assert np.all(np.abs(got - ref) <= tol), (got - ref, tol)
+
+
+def test_tfim_n8_k8_and_exact(ctx):
+    g = json.load(open(os.path.join(GOLD, "tfim_n8.json")))
+    c = I.tfim_n8()
+    _close(ctx, ctx.solve_chain(c), np.array(g["energies_k8"]))
+    c.k = 16
+    _close(ctx, ctx.solve_chain(c), np.array(g["exact"]))
+
+
+def test_xxz_n32_k64(ctx):
+    g = json.load(open(os.path.join(GOLD, "xxz_n32_k64.json")))
+    _close(ctx, ctx.solve_chain(I.xxz_n32()), np.array(g["energies"]))
+
+
+@pytest.mark.parametrize("chain", [
+    I.tfim(10, 1.0, 0.7, 5, 32, 6),                      # full k: exact
+    I.tfim(7, 1.0, 1.3, 2, 128, 6),                      # unbalanced tree
+    I.tfim(16, 1.0, 0.7, 4, 16, 4),
+    I.tfim(24, 1.0, 1.4, 3, 32, 4),                      # L0 = 3 leaves
+    I.xxz(12, list(np.random.default_rng(1).uniform(0.5, 1.5, 11)), 1.0, 3, 24, 6),
+    I.xxz(8, [1.0] * 7, 1.0, 4, 16, 8, fields=[0.5, -1.2, 1.9, 0.1, -0.7, 1.1, -1.8, 0.3]),
+    I.tfim(3, 1.0, 0.5, 4, 8, 3),                        # a single leaf is the whole chain
+])
+def test_chain_matches_oracle(ctx, chain):
+    _close(ctx, ctx.solve_chain(chain), O.solve(chain).energies)
+
+
+def test_full_k_tfim_matches_free_fermions(ctx):
+    c = I.tfim(12, 1.0, 0.9, 3, 64, 8)
+    _close(ctx, ctx.solve_chain(c), CF.tfim_lowest(12, 1.0, 0.9, 8))
+
+
+def test_truncated_energies_are_upper_bounds(ctx):
+    c = I.tfim(32, 1.0, 0.7, 4, 16, 4)
+    E = ctx.solve_chain(c)
+    assert np.all(E >= CF.tfim_lowest(32, 1.0, 0.7, 4) - 1e-9)

@@ -1,0 +1,192 @@
+"""Per-step parity of the GPU path against the oracle on identical inputs.
+
+* Leaf build (Algorithm 1, first step) from Pauli terms.
+* One merge (Algorithm 1, inner loop) on blocks imported from the oracle:
+  retained energies, the cut, the retained subspace (gauge-invariant overlap)
+  and the rotated operators.
+* Edge cases: no coupling term (J' = 0, Eq. (7) without V), ragged k_A != k_B,
+  the dense case k_A k_B <= block size, a top merge, invalid inputs, the
+  memory budget and the iteration cap.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import rmc_oracle as O
+from tests.gpu_util import overlap_singular_values, torch_cuda
+
+import paper_2609_02394_b300 as P
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-10, 1e-9), "mixed": (1e-8, 1e-7)}
+
+
+@pytest.fixture(scope="module", params=["fp64", "mixed"])
+def ctx(request):
+    torch_cuda()
+    c = P.Context(precision=request.param)
+    yield c
+    c.close()
+
+
+def _import(ctx, blk):
+    keys = sorted(blk.ops)
+    h = ctx.block_import(blk.E, [blk.ops[k] for k in keys], keys)
+    return h, keys
+
+
+def _leaf_terms(chain, lo, hi):
+    ons = [(s - lo, p, c) for s, p, c in chain.onsite if lo <= s < hi]
+    bnd = [(i - lo, j - lo, a, b, c) for i, j, a, b, c in chain.bonds if lo <= i and j < hi]
+    return ons, bnd
+
+
+@pytest.mark.parametrize("chain,lo,hi", [
+    (I.tfim(8, 1.0, 0.8, 2, 8, 4), 0, 2),
+    (I.tfim(16, 1.0, 0.7, 4, 16, 4), 4, 8),
+    (I.xxz(8, [0.7, 1.1, 0.9, 1.4, 0.6, 1.2, 1.0], 1.0, 4, 16, 8), 4, 8),
+    (I.xxz(8, [1.0] * 7, 1.0, 4, 16, 8, fields=[0.5, -1.2, 1.9, 0.1, -0.7, 1.1, -1.8, 0.3]), 0, 4),
+    (I.xxz(12, [0.9] * 11, 0.5, 6, 40, 8), 0, 6),
+])
+def test_leaf_matches_oracle(ctx, chain, lo, hi):
+    ref = O.leaf_block(chain, lo, hi, chain.k)
+    carry = [(s - lo, p) for s, p in O.boundary_ops(chain, lo, hi)]
+    ons, bnd = _leaf_terms(chain, lo, hi)
+    blk = ctx.build_leaf_pauli(hi - lo, chain.k, ons, bnd, carry)
+    E, ops, basis = blk.export()
+    assert len(E) == len(ref.E)
+    np.testing.assert_allclose(E, ref.E, atol=1e-12 * max(1, np.abs(ref.E).max()))
+    sv = overlap_singular_values(ref.U, basis.T)
+    assert sv.min() >= 1 - 1e-12
+    G = ref.U.T @ basis.T                      # maps the oracle basis onto the GPU one
+    for j, (s, p) in enumerate(carry):
+        o_ref = ref.ops[(s + lo, p)]
+        np.testing.assert_allclose(ops[j], G.T @ o_ref @ G, atol=1e-11)
+    blk.free()
+
+
+def _merge_case(chain, A_rng, B_rng, k, top):
+    A = O.leaf_block(chain, *A_rng, chain.k) if A_rng[1] - A_rng[0] <= chain.leaf_sites else None
+    B = O.leaf_block(chain, *B_rng, chain.k) if B_rng[1] - B_rng[0] <= chain.leaf_sites else None
+    return A, B
+
+
+MERGES = [
+    # chain, A range, B range, keep, top
+    (I.tfim(8, 1.0, 0.8, 2, 8, 4), (0, 2), (2, 4), 8, False),                  # dense: n = 16
+    (I.tfim(10, 1.0, 0.7, 5, 7, 4), (0, 5), (5, 10), 4, True),                 # the paper's 5 + 5 chain, k = 7
+    (I.xxz(8, [0.7, 1.1, 0.9, 1.4, 0.6, 1.2, 1.0], 1.0, 4, 16, 8), (0, 4), (4, 8), 24, False),
+    (I.xxz(16, list(np.random.default_rng(4).uniform(0.5, 1.5, 15)), 1.0, 8, 40, 8), (0, 8), (8, 16), 64, False),
+    (I.xxz(16, [1.0] * 15, 1.0, 8, 36, 8, fields=list(np.random.default_rng(9).uniform(-2, 2, 16))),
+     (0, 8), (8, 16), 48, False),
+    (I.tfim(12, 1.0, 1.1, 6, 50, 6), (0, 6), (6, 12), 6, True),
+]
+
+
+@pytest.mark.parametrize("case", range(len(MERGES)))
+def test_merge_matches_oracle(ctx, case):
+    chain, Ar, Br, keep, top = MERGES[case]
+    A = O.leaf_block(chain, *Ar, chain.k)
+    B = O.leaf_block(chain, *Br, chain.k)
+    ref, rec = O.merge_blocks(chain, A, B, keep, top)
+    hA, kA_keys = _import(ctx, A)
+    hB, kB_keys = _import(ctx, B)
+    terms = [(c, kA_keys.index(ka), kB_keys.index(kb)) for c, ka, kb in O.merge_terms(chain, *Ar, *Br)]
+    keys = O.boundary_ops(chain, Ar[0], Br[1]) if not top else []
+    carry = [(0, kA_keys.index(k)) if k[0] < Ar[1] else (1, kB_keys.index(k)) for k in keys]
+    blk = ctx.couple(hA, hB, terms, keep, carry, top=top)
+    E, ops, basis = blk.export()
+    etol, stol = TOL[ctx.precision]
+    assert len(E) == len(ref.E)
+    np.testing.assert_allclose(E, ref.E, atol=etol * max(1, np.abs(ref.E).max()))
+    sv = overlap_singular_values(ref.U, basis.T)
+    assert sv.min() >= 1 - stol, sv.min()
+    G = ref.U.T @ basis.T
+    for j, key in enumerate(keys):
+        np.testing.assert_allclose(ops[j], G.T @ ref.ops[key] @ G, atol=1e3 * stol)
+    # the retained basis is orthonormal and diagonalises the projected H_eff
+    np.testing.assert_allclose(basis @ basis.T, np.eye(len(E)), atol=1e-12)
+    H = O.effective_hamiltonian(A.E, B.E, [(c, A.ops[ka], B.ops[kb]) for c, ka, kb in
+                                           O.merge_terms(chain, *Ar, *Br)])
+    np.testing.assert_allclose(basis @ H @ basis.T, np.diag(E), atol=1e-10 * max(1, np.abs(E).max()))
+    for h in (blk, hA, hB):
+        h.free()
+
+
+def test_zero_coupling_is_sorted_sums(ctx):
+    c = I.tfim(8, 1.0, 0.8, 4, 16, 20)
+    A = O.leaf_block(c, 0, 4, 16)
+    B = O.leaf_block(c, 4, 8, 16)
+    hA, _ = _import(ctx, A)
+    hB, _ = _import(ctx, B)
+    blk = ctx.couple(hA, hB, [], 20, [], top=True)
+    E = ctx.lowest(blk, 20)
+    sums = np.sort(np.add.outer(A.E, B.E).reshape(-1))[:20]
+    np.testing.assert_allclose(E, sums, atol=1e-10 * max(1, np.abs(sums).max()))
+
+
+def test_homogeneous_reuse_same_block_twice(ctx):
+    """A and B may be the same block (identical modules, the paper's reuse):
+    an interior leaf of a uniform chain carries Z on its first and last site,
+    and the merge couples A's last-site Z to B's first-site Z."""
+    c = I.tfim(8, 1.0, 0.9, 4, 16, 4)
+    ref = O.solve(c).energies
+    U = O.leaf_block(c, 0, 4, 16).U
+    Z = O.pauli_matrix("Z")
+    z0 = U.T @ O.site_operator(Z, 0, 0, 4) @ U
+    z3 = U.T @ O.site_operator(Z, 3, 0, 4) @ U
+    E = O.leaf_block(c, 0, 4, 16).E
+    h = ctx.block_import(E, [z0, z3], [(0, "Z"), (3, "Z")])
+    blk = ctx.couple(h, h, [(-1.0, 1, 0)], 4, [], top=True)
+    tol = (1e-10 if ctx.precision == "fp64" else 1e-8) * np.abs(ref).max()
+    np.testing.assert_allclose(ctx.lowest(blk, 4), ref, atol=tol)
+
+
+def test_invalid_inputs_are_rejected(ctx):
+    H = np.array([[0.0, 1.0], [0.5, 0.0]])
+    with pytest.raises(P.RmcError) as e:
+        ctx.build_leaf(H, 2)
+    assert e.value.status == P.RMC_ERR_INVAL
+    with pytest.raises(P.RmcError) as e:
+        ctx.build_leaf(np.array([[np.nan]]), 1)
+    assert e.value.status == P.RMC_ERR_INVAL
+    with pytest.raises(P.RmcError) as e:
+        ctx.block_import([1.0, 0.0])                       # not ascending
+    assert e.value.status == P.RMC_ERR_INVAL
+    A = ctx.block_import([0.0, 1.0], [np.eye(2)], [(0, "Z")])
+    with pytest.raises(P.RmcError) as e:
+        ctx.couple(A, A, [(1.0, 0, 5)], 2)                 # missing operator
+    assert e.value.status == P.RMC_ERR_INVAL
+    A.free()
+
+
+def test_memory_budget_is_enforced():
+    torch_cuda()
+    with P.Context(precision="fp64", mem_budget=1 << 20) as c:
+        chain = I.xxz(16, [1.0] * 15, 1.0, 8, 40, 8)
+        A = O.leaf_block(chain, 0, 8, 40)
+        B = O.leaf_block(chain, 8, 16, 40)
+        hA, ka = _import(c, A)
+        hB, kb = _import(c, B)
+        terms = [(cc, ka.index(x), kb.index(y)) for cc, x, y in O.merge_terms(chain, 0, 8, 8, 16)]
+        with pytest.raises(P.RmcError) as e:
+            c.couple(hA, hB, terms, 40)
+        assert e.value.status == P.RMC_ERR_NOMEM
+        assert c.mem_in_use() < (1 << 20)
+
+
+def test_iteration_cap_reports_noconv():
+    torch_cuda()
+    with P.Context(precision="fp64", max_iter=1) as c:
+        chain = I.xxz(16, [1.0] * 15, 1.0, 8, 40, 8)
+        A = O.leaf_block(chain, 0, 8, 40)
+        B = O.leaf_block(chain, 8, 16, 40)
+        hA, ka = _import(c, A)
+        hB, kb = _import(c, B)
+        terms = [(cc, ka.index(x), kb.index(y)) for cc, x, y in O.merge_terms(chain, 0, 8, 8, 16)]
+        with pytest.raises(P.RmcError) as e:
+            c.couple(hA, hB, terms, 40)
+        assert e.value.status == P.RMC_ERR_NOCONV
+        blk = c.couple(hA, hB, terms, 40, allow_noconv=True)   # best iterate still returned
+        assert blk.info()[0] >= 1
