@@ -26,8 +26,9 @@ EXPORTED = [
     "rmc_create", "rmc_destroy", "rmc_last_error", "rmc_mem_in_use", "rmc_stats", "rmc_stream",
     "rmc_build_leaf", "rmc_build_leaf_pauli", "rmc_couple", "rmc_lowest", "rmc_solve_chain",
     "rmc_block_free", "rmc_block_info", "rmc_block_export", "rmc_block_import",
-    "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op",
+    "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
 ]
+PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
 
 class RmcError(RuntimeError):
@@ -87,6 +88,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_kron_matvec": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
         "rmc_syev": ([vp, ip, vp, vp, vp], ip),
         "rmc_rotate_op": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
+        "rmc_profile": ([vp, ip], ip),
+        "rmc_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -182,6 +185,19 @@ class Context:
         a, b = ctypes.c_uint64(), ctypes.c_uint64()
         self._check(self.lib.rmc_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.rmc_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (launch groups, kernel launches, ms, algorithmic flops)} since the last read."""
+        out = {}
+        for i, name in enumerate(PROF_KINDS):
+            g, l, ms, fl = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.rmc_profile_read(self.h, i, ctypes.byref(g), ctypes.byref(l), ctypes.byref(ms),
+                                                  ctypes.byref(fl)))
+            out[name] = (g.value, l.value, ms.value, fl.value)
+        return out
 
     def mem_in_use(self) -> int:
         return self.lib.rmc_mem_in_use(self.h)

@@ -311,98 +311,110 @@ __global__ void gauge_kernel(double* __restrict__ C, long n) {
 }
 
 // ---------------------------------------------------------------------------
-// Small dense symmetric eigensolver, one CTA: cyclic parallel Jacobi in FP32
-// with round-robin pairing (all m(m-1)/2 pairs once per sweep, m/2 disjoint
-// rotations per round; each 2x2 block of A updated by one thread as
-// J_k^T A_{kl} J_l).  Eigenvalues ascending into w, eigenvectors as columns of
-// the row-major m x m V.  m <= kMaxSmallDim.  status[0] += 1 if the sweep cap
-// was hit before the off-diagonal norm fell below 1e-6 ||A||_F.
+// Small dense symmetric eigensolver, one CTA of 1024 threads: cyclic parallel
+// Jacobi in FP32 with round-robin pairing (all m(m-1)/2 pairs once per sweep,
+// m/2 disjoint rotations per round; each 2x2 block of A updated by one thread
+// as J_k^T A_kl J_l, warps over block rows and lanes over block columns so the
+// inner loops need no integer division).  Stops when the off-diagonal norm is
+// below 1e-6 ||A||_F, or when a sweep no longer halves it (the FP32 rounding
+// floor).  Eigenvalues ascending into w, eigenvectors as columns of the
+// row-major m x m V.  m <= kMaxSmallDim.  status[0] += 1 if the sweep cap was
+// hit first.
 // ---------------------------------------------------------------------------
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(512) jacobi_kernel(const TI* __restrict__ S, int m, TO* __restrict__ w,
-                                                     TO* __restrict__ V, int* __restrict__ status, int max_sweeps) {
+__global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, int m, TO* __restrict__ w,
+                                                      TO* __restrict__ V, int* __restrict__ status, int max_sweeps) {
   extern __shared__ float smem[];
   const int mm = (m + 1) & ~1;  // even
-  float* A = smem;              // mm x mm
-  float* Vs = A + mm * mm;      // m x mm
+  const int ld = mm + 1;        // padded row stride of A
+  float* A = smem;              // mm x ld
+  float* Vs = A + mm * ld;      // m x mm
   float* cs = Vs + m * mm;      // mm/2
   float* sn = cs + mm / 2;
   int* P = (int*)(sn + mm / 2);
   int* Q = P + mm / 2;
   __shared__ float red[32];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int half = mm / 2;
 
-  for (int e = tid; e < mm * mm; e += nt) {
-    const int i = e / mm, j = e % mm;
-    float v = 0.f;
-    if (i < m && j < m) v = (float)(0.5 * ((double)S[i * m + j] + (double)S[j * m + i]));
-    A[e] = v;
-  }
-  for (int e = tid; e < m * mm; e += nt) Vs[e] = ((e / mm) == (e % mm)) ? 1.f : 0.f;
+  for (int i = warp; i < mm; i += nw)
+    for (int j = lane; j < mm; j += 32) {
+      float v = 0.f;
+      if (i < m && j < m) v = (float)(0.5 * ((double)S[i * m + j] + (double)S[j * m + i]));
+      A[i * ld + j] = v;
+    }
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < mm; j += 32) Vs[i * mm + j] = (i == j) ? 1.f : 0.f;
   __syncthreads();
   float fro = 0.f;
-  for (int e = tid; e < m * mm; e += nt) {
-    const int i = e / mm, j = e % mm;
-    if (j < m) fro += A[i * mm + j] * A[i * mm + j];
-  }
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < m; j += 32) fro += A[i * ld + j] * A[i * ld + j];
   fro = sqrtf(block_sum(fro, red));
   const float target = 1e-6f * fro;
 
-  const int half = mm / 2;
+  float prev = INFINITY;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     float off = 0.f;
-    for (int e = tid; e < m * mm; e += nt) {
-      const int i = e / mm, j = e % mm;
-      if (j < m && j != i) off += A[i * mm + j] * A[i * mm + j];
-    }
+    for (int i = warp; i < m; i += nw)
+      for (int j = lane; j < m; j += 32)
+        if (j != i) off += A[i * ld + j] * A[i * ld + j];
     off = sqrtf(block_sum(off, red));
-    if (off <= target || fro == 0.f) break;
+    if (off <= target || fro == 0.f || (off > 0.5f * prev && off < 1e-4f * fro)) break;
+    prev = off;
     for (int r = 0; r < mm - 1; ++r) {
-      for (int k = tid; k < half; k += nt) {
+      if (tid < half) {
+        const int k = tid;
         int p, q;
         if (k == 0) { p = r; q = mm - 1; }
-        else { p = (r + k) % (mm - 1); q = (r - k + mm - 1) % (mm - 1); }
-        if (p > q) { int t = p; p = q; q = t; }
-        float c = 1.f, s = 0.f;
+        else {
+          p = r + k; if (p >= mm - 1) p -= mm - 1;
+          q = r - k; if (q < 0) q += mm - 1;
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        float c = 1.f, sv = 0.f;
         if (q < m) {
-          const float apq = A[p * mm + q];
+          const float apq = A[p * ld + q];
           if (apq != 0.f) {
-            const float app = A[p * mm + p], aqq = A[q * mm + q];
+            const float app = A[p * ld + p], aqq = A[q * ld + q];
             const float tau = (aqq - app) / (2.f * apq);
             const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
-            s = t * c;
+            sv = t * c;
           }
         }
-        cs[k] = c; sn[k] = s; P[k] = p; Q[k] = q;
+        cs[k] = c; sn[k] = sv; P[k] = p; Q[k] = q;
       }
       __syncthreads();
-      // A <- J^T A J, block by block
-      for (int e = tid; e < half * half; e += nt) {
-        const int k = e / half, l = e % half;
-        const int pk = P[k], qk = Q[k], pl = P[l], ql = Q[l];
-        const float ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
-        const float a00 = A[pk * mm + pl], a01 = A[pk * mm + ql];
-        const float a10 = A[qk * mm + pl], a11 = A[qk * mm + ql];
-        // rows: J_k^T = [[c, -s], [s, c]]
-        const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
-        const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
-        // cols: J_l = [[c, s], [-s, c]]
-        float n00 = b00 * cl - b01 * sl, n01 = b00 * sl + b01 * cl;
-        float n10 = b10 * cl - b11 * sl, n11 = b10 * sl + b11 * cl;
-        if (k == l) { n01 = 0.f; n10 = 0.f; }
-        A[pk * mm + pl] = n00; A[pk * mm + ql] = n01;
-        A[qk * mm + pl] = n10; A[qk * mm + ql] = n11;
+      // A <- J^T A J, one 2x2 block per (k, l)
+      for (int k = warp; k < half; k += nw) {
+        const int pk = P[k], qk = Q[k];
+        const float ck = cs[k], sk = sn[k];
+        for (int l = lane; l < half; l += 32) {
+          const int pl = P[l], ql = Q[l];
+          const float cl = cs[l], sl = sn[l];
+          const float a00 = A[pk * ld + pl], a01 = A[pk * ld + ql];
+          const float a10 = A[qk * ld + pl], a11 = A[qk * ld + ql];
+          const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
+          const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
+          float n00 = b00 * cl - b01 * sl, n01 = b00 * sl + b01 * cl;
+          float n10 = b10 * cl - b11 * sl, n11 = b10 * sl + b11 * cl;
+          if (k == l) { n01 = 0.f; n10 = 0.f; }
+          A[pk * ld + pl] = n00; A[pk * ld + ql] = n01;
+          A[qk * ld + pl] = n10; A[qk * ld + ql] = n11;
+        }
       }
       // V <- V J
-      for (int e = tid; e < m * half; e += nt) {
-        const int row = e / half, l = e % half;
-        const int pl = P[l], ql = Q[l];
-        const float c = cs[l], s = sn[l];
-        const float vp = Vs[row * mm + pl], vq = Vs[row * mm + ql];
-        Vs[row * mm + pl] = c * vp - s * vq;
-        Vs[row * mm + ql] = s * vp + c * vq;
+      for (int row = warp; row < m; row += nw) {
+        float* vr = Vs + row * mm;
+        for (int l = lane; l < half; l += 32) {
+          const int pl = P[l], ql = Q[l];
+          const float c = cs[l], sv = sn[l];
+          const float vp = vr[pl], vq = vr[ql];
+          vr[pl] = c * vp - sv * vq;
+          vr[ql] = sv * vp + c * vq;
+        }
       }
       __syncthreads();
     }
@@ -410,10 +422,10 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const TI* __restrict__ S, i
   if (sweep == max_sweeps && tid == 0 && status) atomicAdd(status, 1);
   // sort eigenvalues ascending (rank sort, ties by index)
   for (int i = tid; i < m; i += nt) {
-    const float di = A[i * mm + i];
+    const float di = A[i * ld + i];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      const float dj = A[j * mm + j];
+      const float dj = A[j * ld + j];
       rank += (dj < di) || (dj == di && j < i);
     }
     w[rank] = (TO)di;
@@ -423,7 +435,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const TI* __restrict__ S, i
 
 inline size_t jacobi_smem_bytes(int m) {
   const int mm = (m + 1) & ~1;
-  return sizeof(float) * ((size_t)mm * mm + (size_t)m * mm + mm) + sizeof(int) * mm;
+  return sizeof(float) * ((size_t)mm * (mm + 1) + (size_t)m * mm + mm) + sizeof(int) * mm;
 }
 
 // Ogita-Aishima refinement (Japan J. Indust. Appl. Math. 35, 2018), the step
@@ -435,7 +447,7 @@ inline size_t jacobi_smem_bytes(int m) {
 // One CTA.  R is overwritten by E.
 __global__ void oa_correction_kernel(double* __restrict__ R, const double* __restrict__ Sp,
                                      const double* __restrict__ A, int m, double* __restrict__ lam,
-                                     int* __restrict__ done) {
+                                     int* __restrict__ done, double* __restrict__ prev_emax) {
   if (*done) return;
   __shared__ double red[32];
   extern __shared__ double sl[];  // m
@@ -467,8 +479,21 @@ __global__ void oa_correction_kernel(double* __restrict__ R, const double* __res
   }
   emax = block_max(emax, red);
   for (int i = tid; i < m; i += blockDim.x) lam[i] = sl[i];
-  // a correction at the rounding level of FP64 leaves V unchanged: stop
-  if (tid == 0 && emax <= 4e-16) *done = 1;
+  // stop once the correction is at the FP64 rounding level, or once it no
+  // longer shrinks quadratically (near-degenerate pairs leave rounding noise of
+  // order u ||A|| / gap that no further step removes)
+  if (tid == 0) {
+    const double pe = *prev_emax;
+    if (emax <= 4e-16 || (emax < 1e-8 && emax > 0.01 * pe)) *done = 1;
+    *prev_emax = emax;
+  }
+}
+
+// E = (I - G) / 2 (m x m): one Newton-Schulz orthonormalisation step
+// V <- V + V E makes V^T V = I up to O(||I - G||^2).
+__global__ void half_identity_minus_kernel(const double* __restrict__ G, int m, double* __restrict__ E) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)
+    E[e] = 0.5 * (((e / m) == (e % m) ? 1.0 : 0.0) - G[e]);
 }
 
 // dst = src (m x m) unless *skip
@@ -507,65 +532,64 @@ __global__ void sort_pairs_kernel(const double* __restrict__ lam, const double* 
 // is then clamped).
 // ---------------------------------------------------------------------------
 template <typename TC, typename TI, typename TO>
-__global__ void __launch_bounds__(512) cholinv_kernel(const TI* __restrict__ G, int m, double shift,
-                                                      TO* __restrict__ Linv, int* __restrict__ status) {
+__global__ void __launch_bounds__(1024) cholinv_kernel(const TI* __restrict__ G, int m, double shift,
+                                                       TO* __restrict__ Linv, int* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
   TC* L = (TC*)smem_raw;  // m x m
   __shared__ TC red[32];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   TC dmax = 0;
   for (int i = tid; i < m; i += nt) dmax = fmax(dmax, (TC)G[i * m + i]);
   dmax = block_max(dmax, red);
   const TC sh = (TC)shift * dmax;
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e / m, j = e % m;
-    L[e] = (j <= i) ? (TC)(0.5 * ((double)G[i * m + j] + (double)G[j * m + i])) + (i == j ? sh : TC(0)) : TC(0);
-  }
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < m; j += 32)
+      L[i * m + j] = (j <= i) ? (TC)(0.5 * ((double)G[i * m + j] + (double)G[j * m + i])) + (i == j ? sh : TC(0))
+                              : TC(0);
   __syncthreads();
   const TC tiny = dmax * (TC)1e-30 + (TC)(sizeof(TC) == 4 ? 1e-37 : 1e-300);
   for (int j = 0; j < m; ++j) {
+    // every thread reads the pivot and scales its own entries of column j
+    TC d = L[j * m + j];
+    bool bad = !(d > tiny);
+    if (bad) d = fmax(dmax, tiny) * (TC)1e-12;
+    const TC ljj = sqrt(d);
+    const TC inv = TC(1) / ljj;
+    __syncthreads();
     if (tid == 0) {
-      TC d = L[j * m + j];
-      if (!(d > tiny)) {
-        if (status) atomicAdd(status, 1);
-        d = fmax(dmax, tiny) * (TC)1e-12;
-      }
-      L[j * m + j] = sqrt(d);
+      L[j * m + j] = ljj;
+      if (bad && status) atomicAdd(status, 1);
     }
+    for (int i = j + 1 + tid; i < m; i += nt) L[i * m + j] *= inv;
     __syncthreads();
-    const TC ljj = L[j * m + j];
-    for (int i = j + 1 + tid; i < m; i += nt) L[i * m + j] /= ljj;
-    __syncthreads();
-    const int rem = m - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-      if (k <= i) L[i * m + k] -= L[i * m + j] * L[k * m + j];
+    for (int i = j + 1 + warp; i < m; i += nw) {
+      const TC lij = L[i * m + j];
+      for (int k = j + 1 + lane; k <= i; k += 32) L[i * m + k] -= lij * L[k * m + j];
     }
     __syncthreads();
   }
-  // forward substitution row by row: for c < i,
-  //   Li[i][c] = -(sum_{t=c}^{i-1} L[i][t] Li[t][c]) / L[i][i],  Li[t][t] = 1 / L[t][t],
-  // with Li[t][c] (c < t) kept at L[c*m + t].
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int i = 1; i < m; ++i) {
-    for (int c = wid; c < i; c += nw) {
-      TC s = 0;
-      for (int t = c + lane; t < i; t += 32) {
-        const TC lit = (t == c) ? TC(1) / L[t * m + t] : L[c * m + t];
-        s += L[i * m + t] * lit;
-      }
-      s = warp_sum(s);
-      if (lane == 0) L[c * m + i] = -s / L[i * m + i];
+  // L^{-1}, one warp per column c, no block-wide synchronisation: for i > c,
+  //   Li[i][c] = -(sum_{t=c}^{i-1} L[i][t] Li[t][c]) / L[i][i],  Li[c][c] = 1 / L[c][c],
+  // with Li[t][c] (t > c) kept at L[c*m + t] (the strict upper triangle).
+  for (int c = warp; c < m; c += nw) {
+    const TC dcc = TC(1) / L[c * m + c];
+    for (int i = c + 1; i < m; ++i) {
+      TC acc = 0;
+      for (int t = c + lane; t < i; t += 32) acc += L[i * m + t] * ((t == c) ? dcc : L[c * m + t]);
+      acc = warp_sum(acc);
+      if (lane == 0) L[c * m + i] = -acc / L[i * m + i];
+      __syncwarp();
     }
-    __syncthreads();
   }
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e / m, c = e % m;
-    TO v = TO(0);
-    if (c == i) v = (TO)(TC(1) / L[i * m + i]);
-    else if (c < i) v = (TO)L[c * m + i];
-    Linv[e] = v;
-  }
+  __syncthreads();
+  for (int i = warp; i < m; i += nw)
+    for (int c = lane; c < m; c += 32) {
+      TO v = TO(0);
+      if (c == i) v = (TO)(TC(1) / L[i * m + i]);
+      else if (c < i) v = (TO)L[c * m + i];
+      Linv[i * m + c] = v;
+    }
 }
 
 inline size_t cholinv_smem_bytes(int m, size_t elt) { return (size_t)m * m * elt; }

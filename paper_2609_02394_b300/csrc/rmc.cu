@@ -58,6 +58,15 @@ struct rmc_ctx {
   int* d_status = nullptr;      // device scratch ints
   double* h_pinned = nullptr;   // pinned host staging (status + thetas)
   std::set<rmc_block*> blocks;
+  // opt-in per-kind timing (rmc_profile)
+  bool prof = false;
+  struct Pending { cudaEvent_t a, b; int kind; uint64_t launches; double flops; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  uint64_t prof_groups[RMC_PROF_KINDS] = {};
+  uint64_t prof_launches[RMC_PROF_KINDS] = {};
+  double prof_ms[RMC_PROF_KINDS] = {};
+  double prof_flops[RMC_PROF_KINDS] = {};
 };
 
 namespace {
@@ -139,6 +148,56 @@ struct Workspace {
 inline unsigned grid1d(long n, int threads = 256) { return (unsigned)std::min<long>(std::max<long>(1, (n + threads - 1) / threads), 148 * 16); }
 
 // ---------------------------------------------------------------------------
+// Opt-in timing: a Scope records an event pair around a launch group.
+// ---------------------------------------------------------------------------
+cudaEvent_t take_event(rmc_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void harvest(rmc_ctx* ctx) {  // call after a stream synchronisation
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->prof_groups[p.kind] += 1;
+      ctx->prof_launches[p.kind] += p.launches;
+      ctx->prof_ms[p.kind] += ms;
+      ctx->prof_flops[p.kind] += p.flops;
+    }
+    ctx->event_pool.push_back(p.a);
+    ctx->event_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  cudaGetLastError();
+}
+
+struct ProfScope {
+  rmc_ctx* ctx;
+  int kind;
+  double flops;
+  uint64_t l0;
+  cudaEvent_t a = nullptr;
+  ProfScope(rmc_ctx* c, int k, double f) : ctx(c), kind(k), flops(f), l0(c->launches) {
+    if (ctx->prof) {
+      a = take_event(ctx);
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = take_event(ctx);
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back({a, b, kind, ctx->launches - l0, flops});
+  }
+};
+
+// ---------------------------------------------------------------------------
 // GEMM front ends on vector-major blocks (a block of nv vectors of length n is
 // a row-major nv x n matrix).
 // ---------------------------------------------------------------------------
@@ -156,6 +215,7 @@ void gemm_small(const T* A, const T* B, const GemmShape& s, int batches, const E
 template <typename T>
 rmc_status gram(rmc_ctx* ctx, Workspace& ws, const T* X1, int nv1, const T* X2, int nv2, long n, T* G,
                 bool symmetrize) {
+  ProfScope ps(ctx, 4, 2.0 * nv1 * nv2 * (double)n);
   const int tiles = (int)(ceil_div(nv1, 64) * ceil_div(nv2, 64));
   int splits = (int)std::min<long>(std::max<long>(1, n / 128), std::max(1, 296 / tiles));
   splits = std::min(splits, 64);
@@ -177,6 +237,7 @@ rmc_status gram(rmc_ctx* ctx, Workspace& ws, const T* X1, int nv1, const T* X2, 
 template <typename T>
 rmc_status combine(rmc_ctx* ctx, const T* W, bool transW, int nvo, int nvi, const T* X, long n, T* Out, T alpha,
                    T beta, const T* Src) {
+  ProfScope ps(ctx, 5, 2.0 * nvo * nvi * (double)n);
   GemmShape s{nvo, (int)n, nvi, transW ? nvo : nvi, n, 0, 0, 1};
   EpiAxpby<T> epi{Out, Src, n, n, 0, 0, alpha, beta};
   if (transW) gemm_big<T, true, false>(W, X, s, 1, epi, ctx->stream);
@@ -212,6 +273,10 @@ template <typename T>
 rmc_status kron_apply(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y, T alpha, T beta, T gamma,
                       const T* Z, T* Tbuf) {
   const int kA = H.kA, kB = H.kB, no = H.n_ops;
+  // algorithmic FLOPs: 2 n_ops kA kB (kA + kB) per vector for the two
+  // contractions plus 3 kA kB for the diagonal term and the scaling
+  ProfScope ps(ctx, sizeof(T) == 8 ? 1 : 0,
+               (double)nv * ((double)2 * no * kA * kB * (kA + kB) + 3.0 * kA * kB));
   if (no > 0) {
     GemmShape s1{nv * kA, no * kB, kB, kB, kB, 0, 0, 1};
     EpiKron1<T> e1{Tbuf, kA, kB, nv};
@@ -237,9 +302,10 @@ rmc_status kron_apply(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y
 template <typename TI, typename TO>
 rmc_status jacobi(rmc_ctx* ctx, const TI* S, int m, TO* w, TO* V) {
   if (m > kMaxSmallDim) return fail(ctx, RMC_ERR_INVAL, "small eigensolver: m=%d exceeds %d", m, kMaxSmallDim);
+  ProfScope ps(ctx, 2, 0.0);
   const size_t sm = jacobi_smem_bytes(m);
   CK(cudaFuncSetAttribute(jacobi_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  jacobi_kernel<TI, TO><<<1, 512, sm, ctx->stream>>>(S, m, w, V, ctx->d_status + 1, 30);
+  jacobi_kernel<TI, TO><<<1, 1024, sm, ctx->stream>>>(S, m, w, V, ctx->d_status + 1, 30);
   CKL();
   return RMC_OK;
 }
@@ -262,8 +328,9 @@ rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, 
 }
 
 rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w, double* V) {
-  double *V0, *V1, *R, *AV, *Sp, *lam;
+  double *V0, *V1, *R, *AV, *Sp, *lam, *pe;
   int* done;
+  TRY(ws.get(&pe, 1));
   TRY(ws.get(&V0, (size_t)m * m));
   TRY(ws.get(&V1, (size_t)m * m));
   TRY(ws.get(&R, (size_t)m * m));
@@ -272,6 +339,7 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
   TRY(ws.get(&lam, (size_t)m));
   TRY(ws.get(&done, 1));
   CK(cudaMemsetAsync(done, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(pe, 0x7f, sizeof(double), ctx->stream));  // a huge previous correction
   TRY((jacobi<double, double>(ctx, S, m, lam, V0)));
   for (int it = 0; it < kOASteps; ++it) {
     TRY((small_mm_skip<true, false>(ctx, V0, V0, m, R, 0.0, nullptr, done)));
@@ -279,13 +347,18 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
     CKL();
     TRY((small_mm_skip<false, false>(ctx, S, V0, m, AV, 0.0, nullptr, done)));
     TRY((small_mm_skip<true, false>(ctx, V0, AV, m, Sp, 0.0, nullptr, done)));
-    oa_correction_kernel<<<1, 512, sizeof(double) * m, ctx->stream>>>(R, Sp, S, m, lam, done);
+    oa_correction_kernel<<<1, 512, sizeof(double) * m, ctx->stream>>>(R, Sp, S, m, lam, done, pe);
     CKL();
     TRY((small_mm_skip<false, false>(ctx, V0, R, m, V1, 1.0, V0, done)));
     copy_unless_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(V1, V0, m * m, done);
     CKL();
   }
-  sort_pairs_kernel<<<1, 256, 0, ctx->stream>>>(lam, V0, m, w, V);
+  // one Newton-Schulz step: exact orthonormality whatever the refinement left
+  TRY((small_mm_skip<true, false>(ctx, V0, V0, m, R, 0.0, nullptr, nullptr)));
+  half_identity_minus_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(R, m, AV);
+  CKL();
+  TRY((small_mm_skip<false, false>(ctx, V0, AV, m, V1, 1.0, V0, nullptr)));
+  sort_pairs_kernel<<<1, 256, 0, ctx->stream>>>(lam, V1, m, w, V);
   CKL();
   return RMC_OK;
 }
@@ -294,6 +367,7 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
 // relative diagonal shift (robust for ill-conditioned filter output).
 template <typename T>
 rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, double shift) {
+  ProfScope ps(ctx, 3, 0.0);
   T *G, *Li;
   TRY(ws.get(&G, (size_t)nv * nv));
   TRY(ws.get(&Li, (size_t)nv * nv));
@@ -301,7 +375,7 @@ rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, dou
     TRY(gram<T>(ctx, ws, X, nv, X, nv, n, G, true));
     const size_t sm = cholinv_smem_bytes(nv, sizeof(T));
     CK(cudaFuncSetAttribute(cholinv_kernel<T, T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    cholinv_kernel<T, T, T><<<1, 512, sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2);
+    cholinv_kernel<T, T, T><<<1, 1024, sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2);
     CKL();
     TRY(combine<T>(ctx, Li, false, nv, nv, X, n, tmp, T(1), T(0), nullptr));
     CK(cudaMemcpyAsync(X, tmp, sizeof(T) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -312,13 +386,14 @@ rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, dou
 // FP64 Cholesky-QR for a nearly orthonormal block: FP32 Cholesky of the FP64
 // Gram matrix, then two first-order FP64 passes (X <- X - F^T X).
 rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long n, double* tmp) {
+  ProfScope ps(ctx, 3, 0.0);
   double *G, *Li;
   TRY(ws.get(&G, (size_t)nv * nv));
   TRY(ws.get(&Li, (size_t)nv * nv));
   TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
   const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
   CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  cholinv_kernel<float, double, double><<<1, 512, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
+  cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
   CKL();
   TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
   CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -335,6 +410,7 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
 rmc_status read_status(rmc_ctx* ctx, int* vals, int count) {
   CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int) * count, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  harvest(ctx);
   std::memcpy(vals, ctx->h_pinned, sizeof(int) * count);
   return RMC_OK;
 }
@@ -345,6 +421,7 @@ rmc_status to_host(rmc_ctx* ctx, const T* d, double* h, int count) {
   if (sizeof(T) * count > kPinnedDoubles * sizeof(double)) return fail(ctx, RMC_ERR_INVAL, "staging too small");
   CK(cudaMemcpyAsync(ctx->h_pinned, d, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  harvest(ctx);
   const T* src = (const T*)ctx->h_pinned;
   for (int i = 0; i < count; ++i) h[i] = (double)src[i];
   return RMC_OK;
@@ -794,6 +871,8 @@ rmc_status rmc_destroy(rmc_ctx* ctx) {
   std::vector<rmc_block*> bl(ctx->blocks.begin(), ctx->blocks.end());
   for (rmc_block* b : bl) free_block(ctx, b);
   cudaStreamSynchronize(ctx->stream);
+  harvest(ctx);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -810,6 +889,26 @@ rmc_status rmc_stats(const rmc_ctx* ctx, uint64_t* launches, uint64_t* iteration
   if (!ctx) return RMC_ERR_INVAL;
   if (launches) *launches = ctx->launches;
   if (iterations) *iterations = ctx->iterations;
+  return RMC_OK;
+}
+
+rmc_status rmc_profile(rmc_ctx* ctx, int enable) {
+  if (!ctx) return RMC_ERR_INVAL;
+  ctx->prof = enable != 0;
+  return RMC_OK;
+}
+
+rmc_status rmc_profile_read(rmc_ctx* ctx, int kind, uint64_t* groups, uint64_t* launches, double* ms,
+                            double* flops) {
+  if (!ctx || kind < 0 || kind >= RMC_PROF_KINDS) return RMC_ERR_INVAL;
+  cudaStreamSynchronize(ctx->stream);
+  harvest(ctx);
+  if (groups) *groups = ctx->prof_groups[kind];
+  if (launches) *launches = ctx->prof_launches[kind];
+  if (ms) *ms = ctx->prof_ms[kind];
+  if (flops) *flops = ctx->prof_flops[kind];
+  ctx->prof_groups[kind] = ctx->prof_launches[kind] = 0;
+  ctx->prof_ms[kind] = ctx->prof_flops[kind] = 0;
   return RMC_OK;
 }
 
@@ -947,6 +1046,7 @@ rmc_status rmc_couple(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B, cons
                                                         : couple_impl<float>(ctx, in, out, &soft);
   if (st != RMC_OK) return st;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  harvest(ctx);
   if (e != cudaSuccess) return fail(ctx, RMC_ERR_CUDA, "rmc_couple: %s", cudaGetErrorString(e));
   return soft;
 }
