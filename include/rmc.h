@@ -236,6 +236,38 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
                            const double* coef, const void* X, void* Y, const void* Z,
                            double alpha, double beta, double gamma);
 
+/* Allocation-free variant of rmc_kron_matvec, for callers that cannot call
+ * cudaMalloc: a plug-in running inside a host application that reserved the
+ * device memory for its own allocator, or a latency-critical loop that must
+ * not allocate because cudaMalloc and cudaFree can synchronise the device and
+ * stall every stream.  The paper has no counterpart; this is a service of the
+ * library, not a step of the method.
+ *
+ * Same arguments and result as rmc_kron_matvec, but no context: it runs on the
+ * CURRENT device, on `stream` (a cudaStream_t of that device; NULL = the legacy
+ * default stream), and never allocates.  Its scratch (the scaled operator
+ * concatenation and the stage-one products) lives in one fixed device array of
+ * RMC_NOALLOC_SCRATCH_BYTES (16 MiB) inside the library, which every GPU that
+ * loads the library holds until the process exits.  The bytes needed are
+ *   sizeof(T) * n_ops * kA * kA, rounded up to 256, plus sizeof(T) * n_ops * kA * kB * nv
+ * (T = double for dtype 0, float for dtype 1); a larger request returns
+ * RMC_ERR_NOMEM and launches nothing.  Bad arguments return RMC_ERR_INVAL, a
+ * failed CUDA call RMC_ERR_CUDA (there is no context to hold error text).
+ *
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current) and caches it; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents; every scratch element a call reads is first
+ * written by that same call, so nothing has to be cleared.  Calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * the array: order them on one stream or synchronise between them.  Does not
+ * synchronise. */
+#define RMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+rmc_status rmc_kron_matvec_noalloc(void* stream, int dtype, int kA, int kB, int n_ops, int nv,
+                                   const void* EA, const void* EB, const void* A, const void* B,
+                                   const double* coef, const void* X, void* Y, const void* Z,
+                                   double alpha, double beta, double gamma);
+
 /* Lowest eigenpairs of a symmetric m x m FP64 matrix (device pointers): all m
  * eigenvalues ascending into w[m], eigenvectors as columns of the row-major
  * m x m matrix V.  FP32 parallel Jacobi followed by FP64 refinement of the

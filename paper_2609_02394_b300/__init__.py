@@ -27,6 +27,7 @@ EXPORTED = [
     "rmc_build_leaf", "rmc_build_leaf_pauli", "rmc_couple", "rmc_lowest", "rmc_solve_chain",
     "rmc_block_free", "rmc_block_info", "rmc_block_export", "rmc_block_import",
     "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
+    "rmc_kron_matvec_noalloc",
 ]
 PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_syev": ([vp, ip, vp, vp, vp], ip),
         "rmc_rotate_op": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
         "rmc_profile": ([vp, ip], ip),
+        "rmc_kron_matvec_noalloc": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
         "rmc_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
     }
     for name, (args, res) in sig.items():
@@ -97,6 +99,21 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         f.restype = res
     _lib = lib
     return lib
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def kron_matvec_noalloc(stream: int, dtype: int, kA: int, kB: int, n_ops: int, nv: int, EA: int, EB: int, A: int,
+                        B: int, coef, X: int, Y: int, Z: int = 0, alpha: float = 1.0, beta: float = 0.0,
+                        gamma: float = 0.0) -> int:
+    """The allocation-free Kronecker-form product (device pointers, current
+    device, no context).  Returns the rmc_status code."""
+    lib = load_library()
+    c = np.ascontiguousarray(coef if len(coef) else [0.0], dtype=np.float64)
+    return lib.rmc_kron_matvec_noalloc(stream or None, dtype, kA, kB, n_ops, nv, EA, EB, A or None, B or None,
+                                       c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), X, Y, Z or None,
+                                       alpha, beta, gamma)
 
 
 def _dptr(a: np.ndarray):

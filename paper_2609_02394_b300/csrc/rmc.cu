@@ -19,6 +19,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <set>
 #include <string>
@@ -1362,4 +1363,80 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
   if (st != RMC_OK) return st;
   if (soft != RMC_OK) return fail(ctx, soft, "rmc_solve_chain: a merge did not converge");
   return RMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free Kronecker-form product (a library service; the paper has
+// no counterpart).  Its scratch is this fixed device array, not pool memory.
+// In host code `g_noalloc_scratch` is only a handle: the device address comes
+// from cudaGetSymbolAddress, once per device, cached below.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RMC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+cudaError_t noalloc_scratch_address(int device, void** addr) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // the calling thread's current device
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *addr = g_noalloc_addr[device];
+  return cudaSuccess;
+}
+
+template <typename T>
+rmc_status noalloc_kron(cudaStream_t st, int kA, int kB, int n_ops, int nv, const T* EA, const T* EB, const T* A,
+                        const T* B, const double* coef, const T* X, T* Y, const T* Z, double alpha, double beta,
+                        double gamma, unsigned char* scratch) {
+  const size_t acat_bytes = ((sizeof(T) * (size_t)std::max(1, n_ops) * kA * kA + 255) / 256) * 256;
+  T* Acat = (T*)scratch;
+  T* Tbuf = (T*)(scratch + acat_bytes);
+  Coefs cf{};
+  for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
+  if (n_ops > 0) {
+    build_acat_kernel<T><<<grid1d((long)kA * kA * n_ops), 256, 0, st>>>(A, cf, kA, n_ops, Acat);
+    GemmShape s1{nv * kA, n_ops * kB, kB, kB, kB, 0, 0, 1};
+    EpiKron1<T> e1{Tbuf, kA, kB, nv};
+    gemm_big<T, false, true>(X, B, s1, 1, e1, st);
+    GemmShape s2{kA, nv * kB, n_ops * kA, (long)n_ops * kA, (long)nv * kB, 0, 0, 1};
+    EpiKron2<T> e2{X, Z, EA, EB, Y, kA, kB, (T)alpha, (T)beta, (T)gamma};
+    gemm_big<T, false, false>(Acat, Tbuf, s2, 1, e2, st);
+  } else {
+    GemmShape s0{kA, nv * kB, 0, 1, (long)nv * kB, 0, 0, 1};
+    EpiKron2<T> e2{X, Z, EA, EB, Y, kA, kB, (T)alpha, (T)beta, (T)gamma};
+    gemm_big<T, false, false>(EA, X, s0, 1, e2, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? RMC_OK : RMC_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" rmc_status rmc_kron_matvec_noalloc(void* stream, int dtype, int kA, int kB, int n_ops, int nv,
+                                              const void* EA, const void* EB, const void* A, const void* B,
+                                              const double* coef, const void* X, void* Y, const void* Z,
+                                              double alpha, double beta, double gamma) {
+  if (kA < 1 || kB < 1 || n_ops < 0 || n_ops > kMaxOps || nv < 1 || !EA || !EB || !X || !Y ||
+      (n_ops && (!A || !B || !coef)) || (gamma != 0.0 && !Z) || (dtype != 0 && dtype != 1) || X == Y || Z == Y)
+    return RMC_ERR_INVAL;
+  const size_t elt = dtype == 0 ? sizeof(double) : sizeof(float);
+  const size_t need = ((elt * (size_t)std::max(1, n_ops) * kA * kA + 255) / 256) * 256 +
+                      elt * (size_t)std::max(1, n_ops) * kA * kB * nv;
+  if (need > (size_t)RMC_NOALLOC_SCRATCH_BYTES) return RMC_ERR_NOMEM;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoallocMaxDevices) return RMC_ERR_CUDA;
+  void* scratch = nullptr;
+  if (noalloc_scratch_address(device, &scratch) != cudaSuccess) return RMC_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == 0)
+    return noalloc_kron<double>(st, kA, kB, n_ops, nv, (const double*)EA, (const double*)EB, (const double*)A,
+                                (const double*)B, coef, (const double*)X, (double*)Y, (const double*)Z, alpha, beta,
+                                gamma, (unsigned char*)scratch);
+  return noalloc_kron<float>(st, kA, kB, n_ops, nv, (const float*)EA, (const float*)EB, (const float*)A,
+                             (const float*)B, coef, (const float*)X, (float*)Y, (const float*)Z, alpha, beta, gamma,
+                             (unsigned char*)scratch);
 }
