@@ -16,6 +16,8 @@ p99 per-solve latency and the Kronecker-matvec throughput beside it.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision mixed|fp64] [--batch B]
 
+A step submits the batch to a solve server with ``--slots`` concurrent slots
+(worker threads with their own CUDA streams) and waits for every result.
 Under torchrun every rank solves its own batch of independent instances
 (replicas: the solves shard with no exchange), timing is the max over ranks.
 ``--impl reference`` times the CPU oracle (the reference arm of this build).
@@ -57,8 +59,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tf32"])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -282,66 +285,60 @@ def run_ours(args):
     world, rank, local, pg = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    ctx = P.Context(device=local, precision=args.precision, stream=stream.cuda_stream)
     gold = load_gold()
     seeds = batch_seeds(rank, args.batch, gold.keys())
     chains = [I.xxz_n32(s) for s in seeds]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    srv = P.Server(slots=args.slots, device=local, precision=args.precision)
 
-    def step(record):
-        energies, lat = [], []
-        for ch in chains:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            E = ctx.solve_chain(ch)
-            e1.record(stream)
-            energies.append(E)
-            lat.append((e0, e1))
-        return energies, lat
+    def step():
+        tids = [srv.submit(ch) for ch in chains]
+        return [srv.poll(t, wait=True) for t in tids]
 
     for _ in range(args.warmup):
-        step(False)
+        step()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
     clocks.start()
-    l0, _ = ctx.stats()
-    ctx.profile(True)
-    ctx.profile_read()
+    l0 = srv.stats()["launches"]
+    srv.profile(True)
+    srv.profile_read()
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    step_ms, lat_ms, valid, total = [], [], 0, 0
+    step_ms, lat_ms, queue_ms, valid, total = [], [], [], 0, 0
     e2e_s = 0.0
     for s in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                       # evict the previous step's data from L2
+        flush.zero_()                       # evict the previous step's data from L2
+        torch.cuda.synchronize()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
+        s0.record()
         t0 = time.perf_counter()
-        energies, lat = step(True)
-        s1.record(stream)
-        stream.synchronize()
+        outs = step()
+        torch.cuda.synchronize()            # every slot's stream is idle here
+        s1.record()
+        s1.synchronize()
         e2e_s += time.perf_counter() - t0
         step_ms.append(s0.elapsed_time(s1))
-        for (a, b), E, sd in zip(lat, energies, seeds):
-            lat_ms.append(a.elapsed_time(b))
+        for (E, st, lat, qd), sd in zip(outs, seeds):
+            lat_ms.append(lat)
+            queue_ms.append(qd)
             total += 1
             ref = gold.get(sd)
-            if ref is not None and np.all(np.abs(E - ref) <= RTOL * np.maximum(1.0, np.abs(ref))):
+            if st == 0 and ref is not None and np.all(np.abs(E - ref) <= RTOL * np.maximum(1.0, np.abs(ref))):
                 valid += 1
     torch.cuda.synchronize()
     if pg is not None:
         pg.barrier()
     wall = time.perf_counter() - wall0
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    l1, _ = ctx.stats()
+    prof = srv.profile_read()
+    srv.profile(False)
+    l1 = srv.stats()["launches"]
     clk = clocks.stop()
+    srv.close()
 
     dev_s = sum(step_ms) / 1e3
     max_dev_s = reduce_max(pg, dev_s, dev)
@@ -349,19 +346,27 @@ def run_ours(args):
     valid_all = reduce_sum(pg, valid, dev)
     total_all = reduce_sum(pg, total, dev)
 
-    # dominant kernel group and its roofline (algorithmic FLOPs / event time)
+    # dominant kernel group and the Kronecker product's roofline
+    # (algorithmic FLOPs / summed per-stream event time)
     dom = max(prof.items(), key=lambda kv: kv[1][2])
     kron_key = "kron_fp64" if args.precision == "fp64" else "kron_working"
     kg, kl, kms, kfl = prof[kron_key]
-    measured = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     if args.precision == "fp64":
         peak, bound, peak_src = 1.13, "alu", "FP64 DFMA pipe, 1.13 TFLOP/s measured by a DFMA loop on this part"
+    elif args.precision == "mixed_tf32":
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1800.0}
+        peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+        bound = "tensor"
+        peak_src = ("TF32 tensor peak = measured BF16 burst x nominal TF32/BF16 (1.1/2.25); the 3xTF32 "
+                    "product executes 3 tensor products per useful one, so frac <= 1/3 by construction")
     else:
         peak, bound, peak_src = FP32_SIMT_PEAK_TFLOPS, "alu", "FP32 FMA pipe: 148 SMs x 128 lanes x 2 x 2.032 GHz"
     achieved = (kfl / (kms / 1e3)) / 1e12 if kms > 0 else 0.0
-    breakdown = {k: {"launch_groups": v[0], "launches": v[1], "ms": round(v[2], 3),
-                     "share_of_step": round(v[2] / (sum(step_ms) or 1), 4)} for k, v in prof.items()}
+    whole_gpu = (kfl / dev_s) / 1e12 if dev_s > 0 else 0.0
+    stream_ms = sum(v[2] for v in prof.values())
+    breakdown = {k: {"launch_groups": v[0], "launches": v[1], "stream_ms": round(v[2], 3),
+                     "share": round(v[2] / (stream_ms or 1), 4)} for k, v in prof.items()}
 
     if rank == 0:
         vals = sorted(lat_ms)
@@ -371,20 +376,23 @@ def run_ours(args):
             "metric": METRIC, "value": valid_all / max_dev_s, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_dev_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "dtype": {"mixed": "f32+f64", "mixed_tf32": "tf32x3+f32+f64", "fp64": "f64"}[args.precision],
             "data": "synthetic (seeded XXZ chains, J_i ~ U[0.5,1.5])",
             "config": {"workload": WORKLOAD, "N": 32, "k": 64, "q": 8, "L0": 4, "delta": 1.0,
-                       "batch_per_gpu": args.batch, "precision": args.precision,
-                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
-            "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean(lat_ms)},
+                       "batch_per_gpu": args.batch, "slots": args.slots, "precision": args.precision,
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)",
+                       "timing": "CUDA events after device-wide synchronisation (work spans the slots' streams)"},
+            "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean(lat_ms),
+                           "queue_p50": sorted(queue_ms)[len(queue_ms) // 2]},
             "valid_solves": int(valid_all), "solves": int(total_all),
-            "matvec": {"tflops": achieved, "peak_tflops": peak, "frac": achieved / peak if peak else None,
-                       "launch_groups": kg, "ms": kms},
-            "roofline": {"kernel": "kron_matvec (" + ("FP64" if args.precision == "fp64" else "FP32") +
+            "matvec": {"tflops_per_stream": achieved, "tflops_whole_gpu": whole_gpu, "peak_tflops": peak,
+                       "launch_groups": kg, "stream_ms": kms},
+            "roofline": {"kernel": "kron_matvec (" + {"fp64": "FP64", "mixed": "FP32",
+                                                      "mixed_tf32": "tcgen05 3xTF32"}[args.precision] +
                          " two-stage Kronecker product)", "bound": bound, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
                          "peak_source": peak_src,
-                         "dominant_group": dom[0], "dominant_ms": round(dom[1][2], 3)},
+                         "dominant_group": dom[0], "dominant_share": round(dom[1][2] / (stream_ms or 1), 4)},
             "breakdown": breakdown,
             "e2e": {"value": valid_all / max_e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(chain_bytes(c) for c in chains)),
@@ -399,7 +407,6 @@ def run_ours(args):
                                     "sample": f"one solve of seed {seeds[0]}: leaves + {sampled} of {n_m} merges "
                                               f"timed once each" + (", rest extrapolated" if sampled < n_m else "")}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if pg is not None:
         pg.destroy_process_group()
 

@@ -55,10 +55,11 @@ typedef enum rmc_precision {
   /* Every floating-point step in FP64 (DFMA): the plain per-solve form. */
   RMC_PREC_FP64 = 0,
   /* Filter, orthogonalisation and Rayleigh-Ritz of the subspace iteration in
-   * FP32 (FP32 accumulation); every merge then ends with the FP64
-   * finalisation (FP64 Cholesky-QR, FP64 Rayleigh-Ritz with refined
-   * eigenvectors, FP64 rotation), so energies and retained bases are FP64-
-   * consistent projections. */
+   * FP32 (FP32 accumulation); every merge then refines the converged block
+   * with one FP64 Chebyshev filter pass and ends with the FP64 finalisation
+   * (FP64 Cholesky-QR, FP64 Rayleigh-Ritz with refined eigenvectors, FP64
+   * rotation), so energies and retained bases are FP64-consistent
+   * projections. */
   RMC_PREC_MIXED = 1,
   /* As RMC_PREC_MIXED with the Kronecker products of the filter on the tcgen05
    * tensor cores (TF32 operands, FP32 accumulation). */
@@ -200,6 +201,69 @@ rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, int q,
                            const char* bond_pauli_i, const char* bond_pauli_j,
                            const double* bond_coef, double* E_out);
 
+/* ---- many solves at once: batched and served (continuous batching) -------- */
+
+/* A chain Hamiltonian for the solve calls below (same fields as
+ * rmc_solve_chain's arguments; arrays are read at submission and copied). */
+typedef struct rmc_chain {
+  int n_sites, L0, k, q;
+  int n_onsite;
+  const int* onsite_site;
+  const char* onsite_pauli;
+  const double* onsite_coef;
+  int n_bonds;
+  const int* bond_i;
+  const int* bond_j;
+  const char* bond_pauli_i;
+  const char* bond_pauli_j;
+  const double* bond_coef;
+} rmc_chain;
+
+typedef struct rmc_server rmc_server;
+
+/* A solve server: `slots` solves run at once, each on its own host worker
+ * thread, CUDA stream and memory pool, so their kernels overlap on the device.
+ * Independent solves are whole units of Algorithm 1 (its merges within a
+ * level and separate parameter points never exchange data).  Requests are
+ * admitted in arrival order as soon as a slot is free AND their estimated
+ * device memory fits in cfg->mem_budget (shared by all slots; 0 = 40 GiB);
+ * requests that arrive while others run join as those finish (continuous
+ * batching).  cfg->stream is ignored.  Results stay on the device between the
+ * levels of a solve; only energies come back. */
+rmc_status rmc_server_create(const rmc_config* cfg, int slots, rmc_server** out);
+/* Stop accepting work, finish what was admitted or queued, join the workers. */
+rmc_status rmc_server_destroy(rmc_server* srv);
+/* Queue one solve; *id receives its ticket.  RMC_ERR_NOMEM at once if the
+ * request alone can never fit the budget; RMC_ERR_INVAL for a malformed chain. */
+rmc_status rmc_submit(rmc_server* srv, const rmc_chain* chain, uint64_t* id);
+/* Result of a ticket.  wait != 0 blocks until it is done.  *done = 1 when the
+ * result is ready: then E_out[q] (may be NULL) gets the energies,
+ * *solve_status the solve's rmc_status, *latency_ms the time from submission
+ * to completion and *queue_ms the time from submission to admission (each
+ * pointer may be NULL), and the ticket is released.  *done = 0: still queued
+ * or running.  RMC_ERR_INVAL for an unknown ticket. */
+rmc_status rmc_poll(rmc_server* srv, uint64_t id, int wait, int* done, double* E_out, int* solve_status,
+                    double* latency_ms, double* queue_ms);
+/* Text of the most recent failed solve on this server ("" if none). */
+const char* rmc_server_last_error(rmc_server* srv);
+/* Counters: submitted, completed, running, queued, bytes reserved by admitted
+ * solves, kernel launches issued by all slots. */
+rmc_status rmc_server_stats(rmc_server* srv, uint64_t* submitted, uint64_t* completed, int* running,
+                            int* queued, size_t* reserved_bytes, uint64_t* launches);
+/* rmc_profile / rmc_profile_read over every slot of a server (summed).  The
+ * times are per-stream event intervals, so under concurrency they include the
+ * time a launch waited for SMs that other slots held. */
+rmc_status rmc_server_profile(rmc_server* srv, int enable);
+rmc_status rmc_server_profile_read(rmc_server* srv, int kind, uint64_t* groups, uint64_t* launches, double* ms,
+                                   double* flops);
+/* Estimated peak device memory of one solve (what admission reserves). */
+size_t rmc_estimate_bytes(const rmc_chain* chain, int precision);
+/* Solve n chains with `slots` concurrent slots and wait: E_out is n x q_max
+ * row-major (entries past a chain's q are NaN), status_out[n] the per-solve
+ * status.  Returns the first non-OK solve status, else RMC_OK. */
+rmc_status rmc_solve_chains(const rmc_config* cfg, int slots, int n, const rmc_chain* chains, int q_max,
+                            double* E_out, int* status_out);
+
 /* ---- blocks -------------------------------------------------------------- */
 
 rmc_status rmc_block_free(rmc_ctx* ctx, rmc_block* blk);
@@ -227,8 +291,10 @@ rmc_status rmc_block_import(rmc_ctx* ctx, int k, const double* E, int n_ops,
  * with D[a][b] = EA[a] + EB[b].  X, Y, Z: nv x kA x kB (Z may be NULL when
  * gamma == 0; Y must not alias X or Z); A: n_ops x kA x kA; B: n_ops x kB x kB;
  * EA[kA], EB[kB], coef[n_ops]: all device pointers of `dtype` (0 = FP64,
- * 1 = FP32; coef, alpha, beta, gamma are always double on the host side and
- * coef is a host array).  The intermediate products are held in scratch
+ * 1 = FP32 on the FP32 pipe, 2 = FP32 data on the tcgen05 tensor cores in the
+ * 3xTF32 form, which needs 1 <= n_ops, n_ops * kB <= 256 and kA <= 256, else
+ * RMC_ERR_INVAL; coef, alpha, beta, gamma are always double on the host side
+ * and coef is a host array).  The intermediate products are held in scratch
  * memory the library allocates from the context (RMC_ERR_NOMEM if the budget
  * is exceeded).  Runs on the context stream; does not synchronise. */
 rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv,

@@ -27,7 +27,9 @@ EXPORTED = [
     "rmc_build_leaf", "rmc_build_leaf_pauli", "rmc_couple", "rmc_lowest", "rmc_solve_chain",
     "rmc_block_free", "rmc_block_info", "rmc_block_export", "rmc_block_import",
     "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
-    "rmc_kron_matvec_noalloc",
+    "rmc_kron_matvec_noalloc", "rmc_server_create", "rmc_server_destroy", "rmc_submit", "rmc_poll",
+    "rmc_server_stats", "rmc_estimate_bytes", "rmc_solve_chains", "rmc_server_profile",
+    "rmc_server_profile_read", "rmc_server_last_error",
 ]
 PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
@@ -54,6 +56,31 @@ class rmc_term(ctypes.Structure):
 
 class rmc_carry(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int), ("op", ctypes.c_int)]
+
+
+class rmc_chain(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int), ("L0", ctypes.c_int), ("k", ctypes.c_int), ("q", ctypes.c_int),
+                ("n_onsite", ctypes.c_int), ("onsite_site", ctypes.POINTER(ctypes.c_int)),
+                ("onsite_pauli", ctypes.c_char_p), ("onsite_coef", ctypes.POINTER(ctypes.c_double)),
+                ("n_bonds", ctypes.c_int), ("bond_i", ctypes.POINTER(ctypes.c_int)),
+                ("bond_j", ctypes.POINTER(ctypes.c_int)), ("bond_pauli_i", ctypes.c_char_p),
+                ("bond_pauli_j", ctypes.c_char_p), ("bond_coef", ctypes.POINTER(ctypes.c_double))]
+
+
+def make_chain(chain):
+    """An rmc_chain for an instances.Chain-like description; the returned
+    tuple's second item keeps the marshalled arrays alive."""
+    ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    ons, bnd = chain.onsite, chain.bonds
+    keep = [np.array([t[0] for t in ons] or [0], dtype=np.int32), "".join(t[1] for t in ons).encode(),
+            np.array([t[2] for t in ons] or [0.0], dtype=np.float64),
+            np.array([t[0] for t in bnd] or [0], dtype=np.int32), np.array([t[1] for t in bnd] or [0], dtype=np.int32),
+            "".join(t[2] for t in bnd).encode(), "".join(t[3] for t in bnd).encode(),
+            np.array([t[4] for t in bnd] or [0.0], dtype=np.float64)]
+    c = rmc_chain(chain.n_sites, chain.leaf_sites, chain.k, chain.q, len(ons), keep[0].ctypes.data_as(ip), keep[1],
+                  keep[2].ctypes.data_as(dp), len(bnd), keep[3].ctypes.data_as(ip), keep[4].ctypes.data_as(ip),
+                  keep[5], keep[6], keep[7].ctypes.data_as(dp))
+    return c, keep
 
 
 _lib = None
@@ -90,6 +117,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_syev": ([vp, ip, vp, vp, vp], ip),
         "rmc_rotate_op": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
         "rmc_profile": ([vp, ip], ip),
+        "rmc_server_create": ([P(rmc_config), ip, P(vp)], ip),
+        "rmc_server_destroy": ([vp], ip),
+        "rmc_submit": ([vp, P(rmc_chain), P(ctypes.c_uint64)], ip),
+        "rmc_poll": ([vp, ctypes.c_uint64, ip, P(ip), P(dp), P(ip), P(dp), P(dp)], ip),
+        "rmc_server_stats": ([vp, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ip), P(ip), P(ctypes.c_size_t),
+                              P(ctypes.c_uint64)], ip),
+        "rmc_estimate_bytes": ([P(rmc_chain), ip], ctypes.c_size_t),
+        "rmc_server_profile": ([vp, ip], ip),
+        "rmc_server_last_error": ([vp], cp),
+        "rmc_server_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
+        "rmc_solve_chains": ([P(rmc_config), ip, ip, P(rmc_chain), ip, P(dp), P(ip)], ip),
         "rmc_kron_matvec_noalloc": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
         "rmc_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
     }
@@ -308,3 +346,110 @@ class Context:
 
     def rotate_op(self, side: int, kA: int, kB: int, kr: int, C: int, o: int, out: int):
         self._check(self.lib.rmc_rotate_op(self.h, side, kA, kB, kr, C, o, out))
+
+
+def _config(device=0, precision="mixed", mem_budget=0, tol=0.0, max_iter=0, guard=0, tau_deg=0.0):
+    return rmc_config(device, None, mem_budget, PRECISIONS[precision], tol, max_iter, guard, tau_deg)
+
+
+def solve_chains(chains, slots: int = 8, **cfg):
+    """Solve many chains with `slots` concurrent solves (native worker threads,
+    one CUDA stream each).  Returns (energies n x q_max with NaN padding,
+    per-solve status codes)."""
+    lib = load_library()
+    n = len(chains)
+    q_max = max(c.q for c in chains)
+    arr = (rmc_chain * max(1, n))()
+    keep = []
+    for i, c in enumerate(chains):
+        arr[i], kp = make_chain(c)
+        keep.append(kp)
+    E = np.full((n, q_max), np.nan)
+    st = np.zeros(n, dtype=np.int32)
+    c = _config(**cfg)
+    lib.rmc_solve_chains(ctypes.byref(c), slots, n, arr, q_max, _dptr(E),
+                         st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return E, st
+
+
+def estimate_bytes(chain, precision: str = "mixed") -> int:
+    c, keep = make_chain(chain)
+    return load_library().rmc_estimate_bytes(ctypes.byref(c), PRECISIONS[precision])
+
+
+class Server:
+    """Continuous-batching solve server (rmc_server_create / rmc_submit / rmc_poll)."""
+
+    def __init__(self, slots: int = 8, **cfg):
+        self.lib = load_library()
+        c = _config(**cfg)
+        h = ctypes.c_void_p()
+        st = self.lib.rmc_server_create(ctypes.byref(c), slots, ctypes.byref(h))
+        if st != RMC_OK:
+            raise RmcError(st, "rmc_server_create failed")
+        self.h = h
+        self.q = {}
+
+    def submit(self, chain) -> int:
+        c, keep = make_chain(chain)
+        tid = ctypes.c_uint64()
+        st = self.lib.rmc_submit(self.h, ctypes.byref(c), ctypes.byref(tid))
+        if st != RMC_OK:
+            raise RmcError(st, "rmc_submit failed")
+        self.q[tid.value] = chain.q
+        return tid.value
+
+    def poll(self, tid: int, wait: bool = False):
+        """None while pending, else (energies, status, latency_ms, queue_ms)."""
+        q = self.q[tid]
+        E = np.full(q, np.nan)
+        done, sst = ctypes.c_int(), ctypes.c_int()
+        lat, qd = ctypes.c_double(), ctypes.c_double()
+        st = self.lib.rmc_poll(self.h, tid, 1 if wait else 0, ctypes.byref(done), _dptr(E), ctypes.byref(sst),
+                               ctypes.byref(lat), ctypes.byref(qd))
+        if st != RMC_OK:
+            raise RmcError(st, "rmc_poll failed")
+        if not done.value:
+            return None
+        del self.q[tid]
+        return E, sst.value, lat.value, qd.value
+
+    def stats(self):
+        a, b, l = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        r, qd, byt = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        self.lib.rmc_server_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r), ctypes.byref(qd),
+                                  ctypes.byref(byt), ctypes.byref(l))
+        return {"submitted": a.value, "completed": b.value, "running": r.value, "queued": qd.value,
+                "reserved_bytes": byt.value, "launches": l.value}
+
+    def last_error(self) -> str:
+        return self.lib.rmc_server_last_error(self.h).decode()
+
+    def profile(self, enable: bool = True):
+        self.lib.rmc_server_profile(self.h, 1 if enable else 0)
+
+    def profile_read(self):
+        out = {}
+        for i, name in enumerate(PROF_KINDS):
+            g, l, ms, fl = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+            self.lib.rmc_server_profile_read(self.h, i, ctypes.byref(g), ctypes.byref(l), ctypes.byref(ms),
+                                             ctypes.byref(fl))
+            out[name] = (g.value, l.value, ms.value, fl.value)
+        return out
+
+    def close(self):
+        if self.h:
+            self.lib.rmc_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,13 +8,14 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "rmc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "rmc.cu"), os.path.join(HERE, "csrc", "server.cpp")]
 OUT = os.path.join(HERE, "librmc.so")
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
     "-Xcompiler", "-fPIC", "-shared",
     "-I", os.path.join(ROOT, "include"),
+    "-Xcompiler", "-pthread",
 ]
 
 
@@ -22,7 +23,7 @@ def _deps():
     files = list(SOURCES)
     for d in (os.path.join(HERE, "csrc"), os.path.join(ROOT, "include")):
         for f in os.listdir(d):
-            if f.endswith((".cu", ".cuh", ".h")):
+            if f.endswith((".cu", ".cuh", ".h", ".cpp")):
                 files.append(os.path.join(d, f))
     return files
 

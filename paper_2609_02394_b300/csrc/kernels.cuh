@@ -64,6 +64,37 @@ struct EpiKron2 {  // m = a, n = v*kB + b
   }
 };
 
+// Tensor-core variant: the stage-1 output is laid out as stage 2's K-major
+// operand, T'[(v, b)][(j, a)], and stage 2 computes Y^T rows (v, b).
+template <typename T>
+struct EpiKron1T {  // m = v*kA + a, n = j*kB + b  ->  T'[(v*kB + b)*(n_ops*kA) + j*kA + a]
+  T* Tbuf;
+  int kA, kB, n_ops;
+  __device__ void operator()(int, int, int m, int n, T acc) const {
+    const int v = m / kA, a = m % kA, j = n / kB, b = n % kB;
+    Tbuf[((long)v * kB + b) * ((long)n_ops * kA) + (long)j * kA + a] = acc;
+  }
+};
+
+template <typename T>
+struct EpiKron2T {  // m = v*kB + b, n = a
+  const T* X;
+  const T* Z;
+  const T* EA;
+  const T* EB;
+  T* Y;
+  int kA, kB;
+  T alpha, beta, gamma;
+  __device__ void operator()(int, int, int m, int n, T acc) const {
+    const int v = m / kB, b = m % kB;
+    const long idx = ((long)v * kA + n) * kB + b;
+    const T x = X[idx];
+    T y = alpha * (acc + (EA[n] + EB[b]) * x) + beta * x;
+    if (gamma != T(0)) y += gamma * Z[idx];
+    Y[idx] = y;
+  }
+};
+
 // Y = alpha * acc + beta * Src (Src may alias nothing written by the GEMM).
 template <typename T>
 struct EpiAxpby {
@@ -531,14 +562,36 @@ __global__ void sort_pairs_kernel(const double* __restrict__ lam, const double* 
 // triangular) in TO.  status[0] += 1 when a pivot was not positive (the pivot
 // is then clamped).
 // ---------------------------------------------------------------------------
+// With `adaptive` set and G already within 1e-3 of the identity, the kernel
+// instead writes the first-order inverse factor I - F^T (F upper triangular,
+// F_ij = E_ij for i < j, F_ii = E_ii / 2, E = G - I), whose error is O(|E|^2).
 template <typename TC, typename TI, typename TO>
 __global__ void __launch_bounds__(1024) cholinv_kernel(const TI* __restrict__ G, int m, double shift,
-                                                       TO* __restrict__ Linv, int* __restrict__ status) {
+                                                       TO* __restrict__ Linv, int* __restrict__ status,
+                                                       int adaptive = 0) {
   extern __shared__ unsigned char smem_raw[];
   TC* L = (TC*)smem_raw;  // m x m
   __shared__ TC red[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  if (adaptive) {
+    TC emax = 0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e % m;
+      emax = fmax(emax, fabs((TC)G[e] - (i == j ? TC(1) : TC(0))));
+    }
+    emax = block_max(emax, red);
+    if (emax < TC(1e-3)) {
+      for (int e = tid; e < m * m; e += nt) {
+        const int i = e / m, j = e % m;
+        TC v = 0;
+        if (j < i) v = -TC(0.5) * ((TC)G[j * m + i] + (TC)G[i * m + j]);
+        else if (j == i) v = TC(1) - TC(0.5) * ((TC)G[i * m + i] - TC(1));
+        Linv[e] = (TO)v;
+      }
+      return;
+    }
+  }
   TC dmax = 0;
   for (int i = tid; i < m; i += nt) dmax = fmax(dmax, (TC)G[i * m + i]);
   dmax = block_max(dmax, red);

@@ -30,6 +30,7 @@
 #include "common.cuh"
 #include "gemm.cuh"
 #include "kernels.cuh"
+#include "umma.cuh"
 
 using namespace rmc;
 
@@ -297,6 +298,53 @@ rmc_status kron_apply(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y
   return RMC_OK;
 }
 
+// Kronecker-form product on the tcgen05 tensor cores (3xTF32, FP32 data).
+// Returns false (and launches nothing) when a stage's shape does not fit the
+// tensor-core kernel; the caller then runs the SIMT product.
+bool tc_fits(int kA, int kB, int n_ops) {
+  int np, g;
+  size_t sm;
+  return n_ops > 0 && umma::plan(n_ops * kB, kB, &np, &g, &sm) && umma::plan(kA, n_ops * kA, &np, &g, &sm);
+}
+
+template <class Epi>
+rmc_status launch_tc(rmc_ctx* ctx, const float* A, long lda, int M, const float* B, long ldb, int N, int K,
+                     const Epi& epi) {
+  int Npad, group;
+  size_t sm;
+  if (!umma::plan(N, K, &Npad, &group, &sm)) return fail(ctx, RMC_ERR_INVAL, "tensor-core plan failed");
+  // process-wide attribute: raise to the limit once, never lower it
+  CK(cudaFuncSetAttribute(umma::gemm_tf32x3_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)umma::kSmemLimit));
+  umma::GemmArgs g{A, lda, M, B, ldb, N, Npad, K, group, ctx->d_status + 3};
+  const int tiles = (M + umma::kRows - 1) / umma::kRows;
+  umma::gemm_tf32x3_kernel<Epi><<<std::min(tiles, 148), umma::kThreads, sm, ctx->stream>>>(g, epi);
+  CKL();
+  return RMC_OK;
+}
+
+rmc_status kron_apply_tc(rmc_ctx* ctx, const KronOp<float>& H, const float* X, int nv, float* Y, float alpha,
+                         float beta, float gamma, const float* Z, float* Tbuf) {
+  const int kA = H.kA, kB = H.kB, no = H.n_ops;
+  ProfScope ps(ctx, 0, (double)nv * ((double)2 * no * kA * kB * (kA + kB) + 3.0 * kA * kB));
+  TRY(launch_tc(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, EpiKron1T<float>{Tbuf, kA, kB, no}));
+  TRY(launch_tc(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA,
+                EpiKron2T<float>{X, Z, H.EA, H.EB, Y, kA, kB, alpha, beta, gamma}));
+  return RMC_OK;
+}
+
+// The working-precision product of the subspace iteration: tensor cores for
+// the TF32 mixed path when the shape fits, SIMT otherwise.
+template <typename T>
+rmc_status kron_work(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y, T alpha, T beta, T gamma,
+                     const T* Z, T* Tbuf) {
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->cfg.precision == RMC_PREC_MIXED_TF32 && tc_fits(H.kA, H.kB, H.n_ops))
+      return kron_apply_tc(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
+  }
+  return kron_apply<T>(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
+}
+
 // ---------------------------------------------------------------------------
 // Small symmetric eigensolvers.
 // ---------------------------------------------------------------------------
@@ -305,7 +353,10 @@ rmc_status jacobi(rmc_ctx* ctx, const TI* S, int m, TO* w, TO* V) {
   if (m > kMaxSmallDim) return fail(ctx, RMC_ERR_INVAL, "small eigensolver: m=%d exceeds %d", m, kMaxSmallDim);
   ProfScope ps(ctx, 2, 0.0);
   const size_t sm = jacobi_smem_bytes(m);
-  CK(cudaFuncSetAttribute(jacobi_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  // The attribute is process-wide and other threads launch this kernel too:
+  // always raise it to the largest size any call can need, never lower it.
+  CK(cudaFuncSetAttribute(jacobi_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)jacobi_smem_bytes(kMaxSmallDim)));
   jacobi_kernel<TI, TO><<<1, 1024, sm, ctx->stream>>>(S, m, w, V, ctx->d_status + 1, 30);
   CKL();
   return RMC_OK;
@@ -364,19 +415,24 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
   return RMC_OK;
 }
 
-// Cholesky-QR of a vector-major block in place: two passes, the first with a
-// relative diagonal shift (robust for ill-conditioned filter output).
+// Cholesky-QR of a vector-major block in place: a Cholesky pass with a small
+// relative diagonal shift (robust for the ill-conditioned filter output), then
+// a second pass that is the first-order correction X <- (I - F^T) X whenever
+// the first left X X^T within 1e-3 of the identity (error O(||E||^2), no
+// second factorisation), else a full second Cholesky pass.
 template <typename T>
 rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, double shift) {
   ProfScope ps(ctx, 3, 0.0);
   T *G, *Li;
   TRY(ws.get(&G, (size_t)nv * nv));
   TRY(ws.get(&Li, (size_t)nv * nv));
+  CK(cudaFuncSetAttribute(cholinv_kernel<T, T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(T))));
+  const size_t sm = cholinv_smem_bytes(nv, sizeof(T));
   for (int pass = 0; pass < 2; ++pass) {
     TRY(gram<T>(ctx, ws, X, nv, X, nv, n, G, true));
-    const size_t sm = cholinv_smem_bytes(nv, sizeof(T));
-    CK(cudaFuncSetAttribute(cholinv_kernel<T, T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    cholinv_kernel<T, T, T><<<1, 1024, sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2);
+    cholinv_kernel<T, T, T><<<1, 1024, sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2,
+                                                          pass == 0 ? 0 : 1);
     CKL();
     TRY(combine<T>(ctx, Li, false, nv, nv, X, n, tmp, T(1), T(0), nullptr));
     CK(cudaMemcpyAsync(X, tmp, sizeof(T) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -393,7 +449,8 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
   TRY(ws.get(&Li, (size_t)nv * nv));
   TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
   const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
-  CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(float))));
   cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
   CKL();
   TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
@@ -545,6 +602,39 @@ struct MergeInput {
   bool top;
 };
 
+// Chebyshev filter (Zhou and Saad's scaled three-term recurrence) of degree
+// deg >= 2 applied to the block X with H X given: damps [a, ub], scaled at
+// theta0.  Uses Y0, Y1, Y2 (b x n each) and leaves the result in *out (one of
+// them); X and HX are left unchanged.
+template <typename W>
+rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX, int b, double theta0, double a,
+                       double ub, int deg, W* Y0, W* Y1, W* Y2, W* Tbuf, W** out) {
+  const long n = H.n();
+  const double e = (ub - a) / 2, c = (ub + a) / 2;
+  double sigma = e / (theta0 - c);
+  const double tau = 2.0 / sigma;
+  // Y1 = (sigma/e) (H X - c X), from the stored H X
+  axpby_kernel<W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(HX, X, (long)b * n, W(sigma / e),
+                                                                 W(-c * sigma / e), Y1);
+  CKL();
+  const W* Yprev = X;
+  W* Ycur = Y1;
+  W* Ynext = Y2;
+  W* spare = Y0;
+  for (int d = 2; d <= deg; ++d) {
+    const double s1 = 1.0 / (tau - sigma);
+    TRY(kron_work<W>(ctx, H, Ycur, b, Ynext, W(2 * s1 / e), W(-2 * s1 * c / e), W(-sigma * s1), Yprev, Tbuf));
+    // rotate: the buffer two steps back is free unless it is X itself
+    W* old_prev = const_cast<W*>(Yprev);
+    Yprev = Ycur;
+    Ycur = Ynext;
+    Ynext = (old_prev == X) ? spare : old_prev;
+    sigma = s1;
+  }
+  *out = Ycur;
+  return RMC_OK;
+}
+
 template <typename W>
 rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_conv, const int* d_idx,
                  double ub, double tol, int max_iter, W* X, W* HX, W* theta, int* iters_out, bool* converged) {
@@ -568,7 +658,7 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
   CKL();
   auto rayleigh_ritz = [&]() -> rmc_status {
     Workspace wl(ctx);
-    TRY(kron_apply<W>(ctx, H, X, b, HX, W(1), W(0), W(0), nullptr, Tbuf));
+    TRY(kron_work<W>(ctx, H, X, b, HX, W(1), W(0), W(0), nullptr, Tbuf));
     TRY(gram<W>(ctx, wl, X, b, HX, b, n, G, true));
     if (fp64) {
       double* w64 = (double*)(void*)theta;
@@ -604,27 +694,9 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
     const double x0 = std::fabs((th[0] - c) / e);
     int deg = (int)std::floor(std::acosh(rho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
     deg = std::max(2, std::min(dmax, deg));
-    double sigma = e / (th[0] - c);
-    const double tau = 2.0 / sigma;
-    // Y1 = (sigma/e) (H X - c X), from the stored H X
-    axpby_kernel<W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(HX, X, (long)b * n, W(sigma / e),
-                                                                   W(-c * sigma / e), Y1);
-    CKL();
-    W* Yprev = X;  // Y_0 = X
-    W* Ycur = Y1;
-    W* Ynext = Y2;
-    W* spare = Y0;
-    for (int d = 2; d <= deg; ++d) {
-      const double s1 = 1.0 / (tau - sigma);
-      TRY(kron_apply<W>(ctx, H, Ycur, b, Ynext, W(2 * s1 / e), W(-2 * s1 * c / e), W(-sigma * s1), Yprev, Tbuf));
-      // rotate: Yprev <- Ycur, Ycur <- Ynext; Ynext gets the old Yprev buffer
-      // unless that is X (kept intact until the filter ends).
-      W* old_prev = Yprev;
-      Yprev = Ycur;
-      Ycur = Ynext;
-      Ynext = (old_prev == X) ? spare : old_prev;
-      sigma = s1;
-    }
+    W* Yout = nullptr;
+    TRY((cheb_filter<W>(ctx, H, X, HX, b, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout)));
+    W* Ycur = Yout;
     // X <- normalised, orthonormalised filter output
     CK(cudaMemcpyAsync(X, Ycur, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
     normalize_kernel<W><<<b, 256, 0, ctx->stream>>>(X, n, nullptr);
@@ -760,6 +832,28 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
       TRY((chfsi<W>(ctx, ws, Hw, b, k_conv, idx, ub, tolw, ctx->cfg.max_iter, Xw, HXw, thw, &iters, &converged)));
       convert_kernel<double, W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(Xw, X64, (long)b * n);
       CKL();
+      // FP64 refinement of the working-precision subspace: one FP64 Chebyshev
+      // filter pass over the converged block (same bounds and degree rule as
+      // the FP32 iteration, capped at 8), which shrinks its residual by the
+      // filter's contraction before the FP64 finalisation.
+      std::vector<double> th32(b);
+      TRY(to_host<W>(ctx, thw, th32.data(), b));
+      const double a = th32[b - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
+      if (e > 0) {
+        Workspace wp(ctx);
+        double *Y0, *Y1, *Y2, *Yout = nullptr;
+        TRY(wp.get(&Y0, (size_t)b * n));
+        TRY(wp.get(&Y1, (size_t)b * n));
+        TRY(wp.get(&Y2, (size_t)b * n));
+        const double x0 = std::fabs((th32[0] - cc) / e);
+        int deg = (int)std::floor(std::acosh(1e3) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+        deg = std::max(2, std::min(8, deg));
+        TRY(kron_apply<double>(ctx, H64, X64, b, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+        TRY((cheb_filter<double>(ctx, H64, X64, HX64, b, th32[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
+        CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        normalize_kernel<double><<<b, 256, 0, ctx->stream>>>(X64, n, nullptr);
+        CKL();
+      }
     }
   }
   // FP64 finalisation: orthonormalise, project, refined small eigensolve, rotate.
@@ -1127,8 +1221,10 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
                            const void* Z, double alpha, double beta, double gamma) {
   TRY(check_ctx(ctx));
   if (kA < 1 || kB < 1 || n_ops < 0 || n_ops > kMaxOps || nv < 1 || !EA || !EB || !X || !Y ||
-      (n_ops && (!A || !B || !coef)) || (gamma != 0.0 && !Z) || (dtype != 0 && dtype != 1) || X == Y || Z == Y)
+      (n_ops && (!A || !B || !coef)) || (gamma != 0.0 && !Z) || dtype < 0 || dtype > 2 || X == Y || Z == Y)
     return fail(ctx, RMC_ERR_INVAL, "rmc_kron_matvec: bad arguments");
+  if (dtype == 2 && !tc_fits(kA, kB, n_ops))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_kron_matvec: shape outside the tensor-core kernel (n_ops*kB, kA <= 256)");
   Workspace ws(ctx);
   Coefs cf{};
   for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
@@ -1149,6 +1245,11 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
       CKL();
     }
     H.Acat = Acat;
+    if constexpr (sizeof(T) == 4) {
+      if (dtype == 2)
+        return kron_apply_tc(ctx, H, (const float*)X, nv, (float*)Y, (float)alpha, (float)beta, (float)gamma,
+                             (const float*)Z, Tbuf);
+    }
     return kron_apply<T>(ctx, H, (const T*)X, nv, (T*)Y, (T)alpha, (T)beta, (T)gamma, (const T*)Z, Tbuf);
   };
   return dtype == 0 ? run(double{}) : run(float{});

@@ -23,6 +23,8 @@ def dump(name, payload):
 
 
 def main():
+    if "--bench-only" in sys.argv:
+        return bench_batch()
     c1 = I.tfim_n8()
     r1 = O.solve(c1)
     c1f = I.tfim_n8(); c1f.k = 16
@@ -43,16 +45,7 @@ def main():
         "merges": [[m.lo, m.mid, m.hi, m.k_ret, m.k_eff] for m in r2.merges],
         "theta_low": [m.theta[: m.k_ret + 8].tolist() for m in r2.merges],
     })
-    # the benchmark batch: eight XXZ N=32 instances with independent bond draws
-    seeds = [I.seed_for(2) + 7919 * i for i in range(8)]
-    batch = []
-    for sd in seeds:
-        ch = I.xxz_n32(sd)
-        batch.append({"seed": sd, "energies": O.solve(ch).energies.tolist()})
-    dump("bench_xxz_n32_k64.json", {
-        "source": "oracle (Algorithm 1, dense eigh): XXZ N=32, Delta=1, J_i~U[0.5,1.5] per seed, L0=4, k=64, q=8",
-        "instances": batch,
-    })
+    bench_batch()
     ff = {}
     for N in (16, 24, 32, 48, 64, 128):
         for h in (0.2, 0.7, 1.0, 2.0):
@@ -60,6 +53,19 @@ def main():
     dump("tfim_free_fermion.json", {
         "source": "free-fermion closed form (singular values of the bidiagonal h/J matrix)",
         "lowest16": ff,
+    })
+
+
+def bench_batch():
+    """The benchmark batch: XXZ N=32 instances with independent bond draws."""
+    seeds = [I.seed_for(2) + 7919 * i for i in range(32)]
+    batch = []
+    for sd in seeds:
+        ch = I.xxz_n32(sd)
+        batch.append({"seed": sd, "energies": O.solve(ch).energies.tolist()})
+    dump("bench_xxz_n32_k64.json", {
+        "source": "oracle (Algorithm 1, dense eigh): XXZ N=32, Delta=1, J_i~U[0.5,1.5] per seed, L0=4, k=64, q=8",
+        "instances": batch,
     })
 
 

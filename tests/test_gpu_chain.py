@@ -16,10 +16,10 @@ import paper_2609_02394_b300 as P
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-RTOL = {"fp64": 1e-10, "mixed": 1e-8}
+RTOL = {"fp64": 1e-10, "mixed": 1e-8, "mixed_tf32": 1e-8}
 
 
-@pytest.fixture(scope="module", params=["fp64", "mixed"])
+@pytest.fixture(scope="module", params=["fp64", "mixed", "mixed_tf32"])
 def ctx(request):
     torch_cuda()
     c = P.Context(precision=request.param)

@@ -39,8 +39,12 @@ def _dense_reference(EA, EB, oA, oB, coef, X, alpha, beta, gamma, Z):
 
 
 @pytest.mark.parametrize("kA,kB,n_ops,nv", SHAPES)
-@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
 def test_kron_matvec_matches_dense_heff(ctx, kA, kB, n_ops, nv, dtype):
+    """dtype 0: FP64; 1: FP32 on the FP32 pipe; 2: FP32 data on the tcgen05
+    tensor cores (3xTF32), defined for n_ops >= 1, n_ops*kB <= 256, kA <= 256."""
+    if dtype == 2 and not (n_ops >= 1 and n_ops * kB <= 256 and kA <= 256):
+        pytest.skip("outside the tensor-core kernel's shapes")
     rng = np.random.default_rng(kA * 1000 + kB * 10 + n_ops + dtype)
     EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
     X = rng.standard_normal((nv, kA, kB))
@@ -57,6 +61,16 @@ def test_kron_matvec_matches_dense_heff(ctx, kA, kB, n_ops, nv, dtype):
         scale = max(1.0, np.abs(ref).max())
         tol = 1e-12 if dtype == 0 else 3e-5
         assert np.abs(got - ref).max() <= tol * scale, (alpha, beta, gamma, np.abs(got - ref).max() / scale)
+
+
+def test_tensor_core_product_rejects_shapes_it_cannot_hold(ctx):
+    kA, kB, n_ops, nv = 8, 130, 2, 2
+    d = [dev(np.zeros(s), np.float32) for s in (kA, kB, (n_ops, kA, kA), (n_ops, kB, kB), (nv, kA, kB), (nv, kA, kB))]
+    torch_cuda().cuda.synchronize()
+    with pytest.raises(P.RmcError) as e:
+        ctx.kron_matvec(2, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(),
+                        [1.0, 1.0], d[4].data_ptr(), d[5].data_ptr())
+    assert e.value.status == P.RMC_ERR_INVAL
 
 
 def test_kron_matvec_without_coupling(ctx):

@@ -19,10 +19,10 @@ import paper_2609_02394_b300 as P
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": (1e-10, 1e-9), "mixed": (1e-8, 1e-7)}
+TOL = {"fp64": (1e-10, 1e-9), "mixed": (1e-8, 1e-7), "mixed_tf32": (1e-8, 1e-7)}
 
 
-@pytest.fixture(scope="module", params=["fp64", "mixed"])
+@pytest.fixture(scope="module", params=["fp64", "mixed", "mixed_tf32"])
 def ctx(request):
     torch_cuda()
     c = P.Context(precision=request.param)
@@ -139,7 +139,7 @@ def test_homogeneous_reuse_same_block_twice(ctx):
     E = O.leaf_block(c, 0, 4, 16).E
     h = ctx.block_import(E, [z0, z3], [(0, "Z"), (3, "Z")])
     blk = ctx.couple(h, h, [(-1.0, 1, 0)], 4, [], top=True)
-    tol = (1e-10 if ctx.precision == "fp64" else 1e-8) * np.abs(ref).max()
+    tol = TOL[ctx.precision][0] * np.abs(ref).max()
     np.testing.assert_allclose(ctx.lowest(blk, 4), ref, atol=tol)
 
 
