@@ -24,6 +24,7 @@ from .rmc_oracle import (  # noqa: F401
     pauli_matrix,
     rotate_operator,
     solve,
+    sparse_exact_lowest,
     split_tree,
 )
 from . import closed_forms  # noqa: F401

@@ -110,6 +110,33 @@ def exact_spectrum(chain: Chain, n_low: Optional[int] = None) -> np.ndarray:
     return w if n_low is None else w[:n_low]
 
 
+def sparse_exact_lowest(chain: Chain, count: int) -> np.ndarray:
+    """Lowest ``count`` eigenvalues of the whole chain from its sparse
+    Hamiltonian (the same Pauli sums as ``block_hamiltonian``, assembled with
+    scipy.sparse Kronecker products) by Lanczos (ARPACK ``eigsh``): exact
+    diagonalisation for chains too large for a dense matrix (N <= ~20)."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import eigsh
+
+    N = chain.n_sites
+
+    def op(mat, site):
+        out = sp.identity(1, format="csr")
+        for s in range(N):
+            out = sp.kron(out, sp.csr_matrix(mat if s == site else _I2), format="csr")
+        return out
+
+    dim = 2 ** N
+    H = sp.csr_matrix((dim, dim))
+    for s, p, c in chain.onsite:
+        H = H + c * op(pauli_matrix(p), s)
+    for i, j, pi, pj, c in chain.bonds:
+        a, b, cc = _bond_real(pi, pj, c)
+        H = H + cc * (op(a, i) @ op(b, j))
+    w = eigsh(H, k=count, which="SA", tol=1e-14, ncv=max(4 * count, 40))[0]
+    return np.sort(w)
+
+
 # --- recursion tree and carried operators ---------------------------------------------
 
 def split_tree(lo: int, hi: int, L0: int):

@@ -527,6 +527,99 @@ __global__ void half_identity_minus_kernel(const double* __restrict__ G, int m, 
     E[e] = 0.5 * (((e / m) == (e % m) ? 1.0 : 0.0) - G[e]);
 }
 
+// Clean-up for a nearly diagonal symmetric S (m x m, FP64): classical Jacobi
+// -- repeatedly the off-diagonal entry of largest magnitude is found and
+// annihilated by an exact rotation -- until every |S_pq| <= tol * ||S||_F or
+// 4m rotations were made.  Ogita-Aishima steps leave exactly this kind of
+// matrix when near-degenerate pairs (gap below their coupling bound) stay
+// unrotated; a handful of exact rotations finishes them.  S lives in shared
+// memory; the rotations are also applied to the columns of V (row-major,
+// global).  lam[i] = S_ii on return.  One CTA.
+__global__ void __launch_bounds__(1024) jacobi_cleanup_kernel(const double* __restrict__ Sin, int m,
+                                                              double* __restrict__ V, double* __restrict__ lam,
+                                                              double tol) {
+  extern __shared__ double S[];  // m x m
+  __shared__ double red[32];
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_p, s_q;
+  __shared__ double s_c, s_s;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  double fro = 0.0;
+  for (int e = tid; e < m * m; e += nt) {
+    const double v = 0.5 * (Sin[e] + Sin[(e % m) * m + e / m]);
+    S[e] = v;
+    fro += v * v;
+  }
+  fro = sqrt(block_sum(fro, red));
+  const double thresh = tol * fro;
+  for (int rot = 0; rot < 4 * m; ++rot) {
+    // argmax |S_pq| over p < q
+    double best = -1.0;
+    int bi = 0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int p = e / m, q = e % m;
+      if (q > p) {
+        const double a = fabs(S[e]);
+        if (a > best) { best = a; bi = e; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { sv[wid] = best; si[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      int w = 0;
+      for (int j = 1; j < (nt >> 5); ++j)
+        if (sv[j] > sv[w] || (sv[j] == sv[w] && si[j] < si[w])) w = j;
+      s_p = si[w] / m;
+      s_q = si[w] % m;
+      sv[0] = sv[w];
+      if (sv[w] > thresh) {
+        const int p = s_p, q = s_q;
+        const double apq = S[p * m + q], app = S[p * m + p], aqq = S[q * m + q];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        s_c = 1.0 / sqrt(1.0 + t * t);
+        s_s = t * s_c;
+      }
+    }
+    __syncthreads();
+    if (!(sv[0] > thresh)) break;
+    const int p = s_p, q = s_q;
+    const double c = s_c, s = s_s;
+    // rows p, q then columns p, q of S (J = [[c, s], [-s, c]] in (p, q)), and V <- V J
+    for (int j = tid; j < m; j += nt) {
+      const double ap = S[p * m + j], aq = S[q * m + j];
+      S[p * m + j] = c * ap - s * aq;
+      S[q * m + j] = s * ap + c * aq;
+    }
+    __syncthreads();
+    for (int j = tid; j < m; j += nt) {
+      const double ap = S[j * m + p], aq = S[j * m + q];
+      S[j * m + p] = c * ap - s * aq;
+      S[j * m + q] = s * ap + c * aq;
+      const double vp = V[j * m + p], vq = V[j * m + q];
+      V[j * m + p] = c * vp - s * vq;
+      V[j * m + q] = s * vp + c * vq;
+    }
+    __syncthreads();
+    if (tid == 0) { S[p * m + q] = 0.0; S[q * m + p] = 0.0; }
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += nt) lam[i] = S[i * m + i];
+}
+
+// V = I (m x m)
+__global__ void identity_fill_kernel(double* __restrict__ V, int m) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)
+    V[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
+}
+
 // dst = src (m x m) unless *skip
 __global__ void copy_unless_kernel(const double* __restrict__ src, double* __restrict__ dst, int count,
                                    const int* __restrict__ skip) {

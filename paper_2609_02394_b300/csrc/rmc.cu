@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -60,6 +61,7 @@ struct rmc_ctx {
   int* d_status = nullptr;      // device scratch ints
   double* h_pinned = nullptr;   // pinned host staging (status + thetas)
   std::set<rmc_block*> blocks;
+  int trace = 0;  // RMC_TRACE=1 in the environment: per-iteration convergence lines on stderr
   // opt-in per-kind timing (rmc_profile)
   bool prof = false;
   struct Pending { cudaEvent_t a, b; int kind; uint64_t launches; double flops; };
@@ -379,7 +381,12 @@ rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, 
   return RMC_OK;
 }
 
-rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w, double* V) {
+// With from_identity the Jacobi start is skipped and the refinement starts
+// from the identity: used when S is already nearly diagonal (the Rayleigh-
+// Ritz matrix of a block whose chunks were each diagonalised), and for any
+// size (no shared-memory bound).
+rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w, double* V,
+                  bool from_identity = false) {
   double *V0, *V1, *R, *AV, *Sp, *lam, *pe;
   int* done;
   TRY(ws.get(&pe, 1));
@@ -392,8 +399,14 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
   TRY(ws.get(&done, 1));
   CK(cudaMemsetAsync(done, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(pe, 0x7f, sizeof(double), ctx->stream));  // a huge previous correction
-  TRY((jacobi<double, double>(ctx, S, m, lam, V0)));
-  for (int it = 0; it < kOASteps; ++it) {
+  if (from_identity || m > kMaxSmallDim) {
+    identity_fill_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(V0, m);
+    CKL();
+  } else {
+    TRY((jacobi<double, double>(ctx, S, m, lam, V0)));
+  }
+  const int steps = (from_identity || m > kMaxSmallDim) ? 2 * kOASteps : kOASteps;
+  for (int it = 0; it < steps; ++it) {
     TRY((small_mm_skip<true, false>(ctx, V0, V0, m, R, 0.0, nullptr, done)));
     identity_minus_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(R, m, done);
     CKL();
@@ -410,6 +423,16 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
   half_identity_minus_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(R, m, AV);
   CKL();
   TRY((small_mm_skip<false, false>(ctx, V0, AV, m, V1, 1.0, V0, nullptr)));
+  // exact rotations for the pairs the refinement left coupled (near-degenerate
+  // pairs whose gap is below its coupling bound): on Sp = V^T S V in FP64
+  if (m <= kMaxSmallDim) {
+    TRY((small_mm_skip<false, false>(ctx, S, V1, m, AV, 0.0, nullptr, nullptr)));
+    TRY((small_mm_skip<true, false>(ctx, V1, AV, m, Sp, 0.0, nullptr, nullptr)));
+    CK(cudaFuncSetAttribute(jacobi_cleanup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(sizeof(double) * kMaxSmallDim * kMaxSmallDim)));
+    jacobi_cleanup_kernel<<<1, 1024, sizeof(double) * m * m, ctx->stream>>>(Sp, m, V1, lam, 1e-14);
+    CKL();
+  }
   sort_pairs_kernel<<<1, 256, 0, ctx->stream>>>(lam, V1, m, w, V);
   CKL();
   return RMC_OK;
@@ -447,15 +470,19 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
   double *G, *Li;
   TRY(ws.get(&G, (size_t)nv * nv));
   TRY(ws.get(&Li, (size_t)nv * nv));
-  TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
-  const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
-  CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(float))));
-  cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
-  CKL();
-  TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
-  CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
-  for (int pass = 0; pass < 2; ++pass) {
+  const bool wide = nv > kMaxSmallDim;  // too wide for the one-CTA factorisation: the block is
+                                        // then orthonormal to working precision, first order suffices
+  if (!wide) {
+    TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
+    const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
+    CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(float))));
+    cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
+    CKL();
+    TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
+    CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  for (int pass = 0; pass < (wide ? 3 : 2); ++pass) {
     TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
     cholqr_first_order_kernel<<<grid1d((long)nv * nv), 256, 0, ctx->stream>>>(G, nv, Li);
     CKL();
@@ -685,6 +712,15 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
     int fails = 0;
     TRY(read_status(ctx, &fails, 1));
     TRY(to_host<W>(ctx, theta, th.data(), b));
+    if (ctx->trace) {
+      std::vector<double> r(b);
+      TRY(to_host<double>(ctx, rn, r.data(), b));
+      int worst = 0;
+      for (int i = 0; i < k_conv; ++i)
+        if (r[i] / std::max(1.0, std::fabs(th[i])) > r[worst] / std::max(1.0, std::fabs(th[worst]))) worst = i;
+      fprintf(stderr, "[rmc] n=%ld b=%d it=%d fails=%d worst i=%d res=%.3e theta=%.12g th0=%.12g thb=%.12g\n", n, b, it,
+              fails, worst, r[worst] / std::max(1.0, std::fabs(th[worst])), th[worst], th[0], th[b - 1]);
+    }
     if (fails == 0) { *converged = true; break; }
     if (it >= max_iter) break;
     ctx->iterations++;
@@ -711,6 +747,123 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
   if (X != X_orig) CK(cudaMemcpyAsync(X_orig, X, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
   if (HX != HX_orig) CK(cudaMemcpyAsync(HX_orig, HX, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
   *iters_out = it;
+  return RMC_OK;
+}
+
+
+// X_a <- X_a - X_l^T (X_l X_a^T)^T, twice: remove the span of the nl locked
+// vectors X_l from the na vectors X_a (classical Gram-Schmidt, two passes).
+template <typename W>
+rmc_status project_out(rmc_ctx* ctx, const W* Xl, int nl, W* Xa, int na, long n, W* C) {
+  if (nl <= 0) return RMC_OK;
+  for (int pass = 0; pass < 2; ++pass) {
+    Workspace wl(ctx);
+    TRY(gram<W>(ctx, wl, Xl, nl, Xa, na, n, C, false));   // C[i][j] = <x_l_i, x_a_j>
+    TRY(combine<W>(ctx, C, true, na, nl, Xl, n, Xa, W(-1), W(1), Xa));
+  }
+  return RMC_OK;
+}
+
+// Chebyshev-filtered subspace iteration with locking, for blocks wider than
+// the small eigensolver: the lowest k_conv eigenpairs are found `chunk` at a
+// time, each chunk in the orthogonal complement of the pairs already locked,
+// with an active block of at most kMaxSmallDim vectors (chunk + 32 guard).
+// On return the first k_conv rows of X are the locked Ritz vectors and the
+// rest (up to b_total) the last chunk's guard vectors; theta holds all b_total
+// Ritz values.
+template <typename W>
+rmc_status chfsi_locked(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b_total, int k_conv, const int* d_idx,
+                        double ub, double tol, int max_iter, W* X, W* HX, W* theta, int* iters_out, bool* converged) {
+  const long n = H.n();
+  constexpr int kGuard = 32;
+  const int chunk = kMaxSmallDim - kGuard;
+  const int bmax = kMaxSmallDim;
+  W *Y0, *Y1, *Y2, *Tbuf, *G, *Z, *tmp, *C;
+  double* rn;
+  TRY(ws.get(&Y0, (size_t)bmax * n));
+  TRY(ws.get(&Y1, (size_t)bmax * n));
+  TRY(ws.get(&Y2, (size_t)bmax * n));
+  TRY(ws.get(&tmp, (size_t)bmax * n));
+  TRY(ws.get(&Tbuf, (size_t)std::max(1, H.n_ops) * bmax * n));
+  TRY(ws.get(&G, (size_t)bmax * bmax));
+  TRY(ws.get(&Z, (size_t)bmax * bmax));
+  TRY(ws.get(&C, (size_t)b_total * bmax));
+  TRY(ws.get(&rn, (size_t)bmax));
+  const bool fp64 = sizeof(W) == 8;
+  const double rho = fp64 ? 1e6 : 1e3;
+  const int dmax = 40;
+  CK(cudaMemsetAsync(X, 0, sizeof(W) * b_total * n, ctx->stream));
+  unit_vectors_kernel<W><<<ceil_div(b_total, 128), 128, 0, ctx->stream>>>(d_idx, b_total, n, X);
+  CKL();
+  *converged = true;
+  int total_it = 0;
+  for (int L = 0; L < k_conv;) {
+    const int c = std::min(chunk, k_conv - L);
+    const int ba = std::min(b_total - L, c + kGuard);
+    W* Xa = X + (size_t)L * n;
+    W* HXa = HX + (size_t)L * n;
+    W* tha = theta + L;
+    auto orthonormalise = [&]() -> rmc_status {
+      TRY(project_out<W>(ctx, X, L, Xa, ba, n, C));
+      normalize_kernel<W><<<ba, 256, 0, ctx->stream>>>(Xa, n, nullptr);
+      CKL();
+      Workspace wl(ctx);
+      return cholqr<W>(ctx, wl, Xa, ba, n, tmp, fp64 ? 1e-14 : 1e-6);
+    };
+    auto rayleigh_ritz = [&]() -> rmc_status {
+      Workspace wl(ctx);
+      TRY(kron_work<W>(ctx, H, Xa, ba, HXa, W(1), W(0), W(0), nullptr, Tbuf));
+      TRY(gram<W>(ctx, wl, Xa, ba, HXa, ba, n, G, true));
+      if (fp64) {
+        TRY(syev64(ctx, wl, (const double*)(const void*)G, ba, (double*)(void*)tha, (double*)(void*)Z));
+      } else {
+        TRY((jacobi<W, W>(ctx, G, ba, tha, Z)));
+      }
+      TRY(combine<W>(ctx, Z, true, ba, ba, Xa, n, tmp, W(1), W(0), nullptr));
+      CK(cudaMemcpyAsync(Xa, tmp, sizeof(W) * ba * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      TRY(combine<W>(ctx, Z, true, ba, ba, HXa, n, tmp, W(1), W(0), nullptr));
+      CK(cudaMemcpyAsync(HXa, tmp, sizeof(W) * ba * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+      residual_kernel<W><<<ba, 256, 0, ctx->stream>>>(Xa, HXa, tha, n, c, tol, rn, ctx->d_status);
+      CKL();
+      return RMC_OK;
+    };
+    TRY(orthonormalise());
+    TRY(rayleigh_ritz());
+    std::vector<double> th(ba);
+    for (int it = 0;; ++it) {
+      int fails = 0;
+      TRY(read_status(ctx, &fails, 1));
+      TRY(to_host<W>(ctx, tha, th.data(), ba));
+      if (ctx->trace) {
+        std::vector<double> r(ba);
+        TRY(to_host<double>(ctx, rn, r.data(), ba));
+        int worst = 0;
+        for (int i = 0; i < c; ++i)
+          if (r[i] / std::max(1.0, std::fabs(th[i])) > r[worst] / std::max(1.0, std::fabs(th[worst]))) worst = i;
+        fprintf(stderr, "[rmc locked] n=%ld L=%d c=%d ba=%d it=%d fails=%d worst i=%d res=%.3e theta=%.12g\n", n, L, c,
+                ba, it, fails, worst, r[worst] / std::max(1.0, std::fabs(th[worst])), th[worst]);
+      }
+      if (fails == 0) break;
+      if (it >= max_iter) { *converged = false; break; }
+      ctx->iterations++;
+      total_it++;
+      const double a = th[ba - 1];
+      const double e = (ub - a) / 2, cc = (ub + a) / 2;
+      if (!(e > 0)) { *converged = false; break; }
+      const double x0 = std::fabs((th[0] - cc) / e);
+      int deg = (int)std::floor(std::acosh(rho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+      deg = std::max(2, std::min(dmax, deg));
+      W* Yout = nullptr;
+      TRY((cheb_filter<W>(ctx, H, Xa, HXa, ba, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout)));
+      CK(cudaMemcpyAsync(Xa, Yout, sizeof(W) * ba * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      TRY(orthonormalise());
+      TRY(rayleigh_ritz());
+    }
+    if (!*converged) break;
+    L += c;
+  }
+  *iters_out = total_it;
   return RMC_OK;
 }
 
@@ -764,8 +917,17 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   const int k_ret = (int)std::min<long>(in.k_keep, n);
   int g = ctx->cfg.guard > 0 ? ctx->cfg.guard : std::max(16, k_ret / 2);
   int b = (int)std::min<long>(n, (long)k_ret + g);
-  b = std::min(b, kMaxSmallDim);
-  if (b < k_ret) return fail(ctx, RMC_ERR_INVAL, "kept count %d exceeds the solver block limit %d", k_ret, kMaxSmallDim);
+  // Blocks wider than the small eigensolver are solved with locking, chunk by
+  // chunk, with a 32-vector guard after the wanted ones.
+  // Single block whenever the wanted vectors and a guard of at least 16 fit
+  // (the guard shrinks to what is left); otherwise locking, chunk by chunk.
+  const int want = in.top ? k_ret : k_ret + 1;
+  const bool chunked = b > kMaxSmallDim && (long)want + 16 > kMaxSmallDim && n > kMaxSmallDim;
+  if (chunked) b = (int)std::min<long>(n, (long)k_ret + 1 + 31);
+  else b = std::min(b, kMaxSmallDim);
+  if (!chunked && b < want && b < n)
+    return fail(ctx, RMC_ERR_INVAL, "kept count %d does not fit the solver block", k_ret);
+  if (b > 1024) return fail(ctx, RMC_ERR_INVAL, "kept count %d exceeds the solver limit of 992", k_ret);
   const int k_conv = std::min(b, in.top ? k_ret : k_ret + 1);
 
   // FP64 operator copies for the diagonal, the finalisation and the rotation
@@ -810,7 +972,8 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   TRY(ws.get(&Tb64, (size_t)std::max(1, no) * b * n));
   bool converged = true;
   int iters = 0;
-  const bool dense = (b == n);
+  std::vector<double> th_work;  // working-precision Ritz values (mixed paths)
+  const bool dense = (b == n) && !chunked;
   if (dense) {
     CK(cudaMemsetAsync(X64, 0, sizeof(double) * b * n, ctx->stream));
     unit_vectors_kernel<double><<<ceil_div(b, 128), 128, 0, ctx->stream>>>(idx, b, n, X64);
@@ -820,7 +983,12 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
     if (sizeof(W) == 8) {
       double* th;
       TRY(ws.get(&th, b));
-      TRY((chfsi<double>(ctx, ws, H64, b, k_conv, idx, ub, tol, ctx->cfg.max_iter, X64, HX64, th, &iters, &converged)));
+      if (chunked)
+        TRY((chfsi_locked<double>(ctx, ws, H64, b, k_conv, idx, ub, tol, ctx->cfg.max_iter, X64, HX64, th, &iters,
+                                  &converged)));
+      else
+        TRY((chfsi<double>(ctx, ws, H64, b, k_conv, idx, ub, tol, ctx->cfg.max_iter, X64, HX64, th, &iters,
+                           &converged)));
     } else {
       KronOp<W> Hw;
       TRY(prepare_kron<W>(ctx, ws, in, &Hw));
@@ -829,51 +997,100 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
       TRY(ws.get(&HXw, (size_t)b * n));
       TRY(ws.get(&thw, b));
       const double tolw = ctx->cfg.precision == RMC_PREC_FP64 ? tol : std::max(tol, 2e-6);
-      TRY((chfsi<W>(ctx, ws, Hw, b, k_conv, idx, ub, tolw, ctx->cfg.max_iter, Xw, HXw, thw, &iters, &converged)));
+      if (chunked)
+        TRY((chfsi_locked<W>(ctx, ws, Hw, b, k_conv, idx, ub, tolw, ctx->cfg.max_iter, Xw, HXw, thw, &iters,
+                             &converged)));
+      else
+        TRY((chfsi<W>(ctx, ws, Hw, b, k_conv, idx, ub, tolw, ctx->cfg.max_iter, Xw, HXw, thw, &iters, &converged)));
       convert_kernel<double, W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(Xw, X64, (long)b * n);
       CKL();
       // FP64 refinement of the working-precision subspace: one FP64 Chebyshev
-      // filter pass over the converged block (same bounds and degree rule as
-      // the FP32 iteration, capped at 8), which shrinks its residual by the
-      // filter's contraction before the FP64 finalisation.
-      std::vector<double> th32(b);
-      TRY(to_host<W>(ctx, thw, th32.data(), b));
+      // filter pass over the converged block (same bounds; degree for an
+      // amplification ratio of 1e6, at most 12), which shrinks its residual by
+      // the filter's contraction before the FP64 finalisation.
+      th_work.resize(b);
+      TRY(to_host<W>(ctx, thw, th_work.data(), b));
+      const std::vector<double>& th32 = th_work;
       const double a = th32[b - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
-      if (e > 0) {
+      if (e > 0 && !chunked) {
         Workspace wp(ctx);
         double *Y0, *Y1, *Y2, *Yout = nullptr;
         TRY(wp.get(&Y0, (size_t)b * n));
         TRY(wp.get(&Y1, (size_t)b * n));
         TRY(wp.get(&Y2, (size_t)b * n));
         const double x0 = std::fabs((th32[0] - cc) / e);
-        int deg = (int)std::floor(std::acosh(1e3) / std::acosh(std::max(x0, 1.0 + 1e-12)));
-        deg = std::max(2, std::min(8, deg));
+        int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+        deg = std::max(2, std::min(12, deg));
         TRY(kron_apply<double>(ctx, H64, X64, b, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
         TRY((cheb_filter<double>(ctx, H64, X64, HX64, b, th32[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
         CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
         normalize_kernel<double><<<b, 256, 0, ctx->stream>>>(X64, n, nullptr);
         CKL();
+        // the filtered block can be conditioned up to the filter's ratio: FP64 factorisation
+        TRY(cholqr<double>(ctx, wp, X64, b, n, tmp64, 1e-14));
       }
     }
   }
-  // FP64 finalisation: orthonormalise, project, refined small eigensolve, rotate.
-  TRY(cholqr64_refine(ctx, ws, X64, b, n, tmp64));
-  TRY(kron_apply<double>(ctx, H64, X64, b, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
-  double *Gs, *w, *Zs;
-  TRY(ws.get(&Gs, (size_t)b * b));
-  TRY(ws.get(&w, b));
-  TRY(ws.get(&Zs, (size_t)b * b));
-  TRY(gram<double>(ctx, ws, X64, b, HX64, b, n, Gs, true));
-  TRY(syev64(ctx, ws, Gs, b, w, Zs));
-  double* C = tmp64;
-  TRY(combine<double>(ctx, Zs, true, b, b, X64, n, C, 1.0, 0.0, nullptr));
-  std::vector<double> th(b);
-  TRY(to_host<double>(ctx, w, th.data(), b));
-  int keff = k_ret;
-  if (!in.top && k_ret < n) {
-    std::vector<double> tfull(th.begin(), th.begin() + std::min<long>(b, n));
-    keff = cut_rule(tfull, k_ret, ctx->cfg.tau_deg);
+  // FP64 finalisation: orthonormalise, project, refined small eigensolve, on
+  // the whole block (the guard vectors improve the Rayleigh-Ritz extraction of
+  // the wanted subspace: restricting it to the wanted vectors cost accuracy).
+  const int bf = b;
+  if (chunked) {
+    // Chunk by chunk (at most 128 vectors each): the FP64 filter pass of the
+    // mixed paths, removal of the earlier chunks' span, FP64 Cholesky-QR and a
+    // chunk Rayleigh-Ritz.  The global Rayleigh-Ritz below is then nearly
+    // diagonal and its refinement starts from the identity.
+    const int cw = 128;
+    Workspace wc(ctx);
+    double *Y0, *Y1, *Y2, *Cp, *Gc, *Zc, *wcv;
+    TRY(wc.get(&Y0, (size_t)cw * n));
+    TRY(wc.get(&Y1, (size_t)cw * n));
+    TRY(wc.get(&Y2, (size_t)cw * n));
+    TRY(wc.get(&Cp, (size_t)bf * cw));
+    TRY(wc.get(&Gc, (size_t)cw * cw));
+    TRY(wc.get(&Zc, (size_t)cw * cw));
+    TRY(wc.get(&wcv, cw));
+    const bool polish = sizeof(W) == 4 && th_work.size() == (size_t)bf;
+    for (int s0 = 0; s0 < bf; s0 += cw) {
+      const int nc = std::min(cw, bf - s0);
+      double* Xc = X64 + (size_t)s0 * n;
+      if (polish && nc >= 2) {
+        const double a = th_work[s0 + nc - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
+        if (e > 0) {
+          const double x0 = std::fabs((th_work[s0] - cc) / e);
+          int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+          deg = std::max(2, std::min(12, deg));
+          double* Yout = nullptr;
+          TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+          TRY((cheb_filter<double>(ctx, H64, Xc, HX64, nc, th_work[s0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
+          CK(cudaMemcpyAsync(Xc, Yout, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+      }
+      TRY(project_out<double>(ctx, X64, s0, Xc, nc, n, Cp));
+      normalize_kernel<double><<<nc, 256, 0, ctx->stream>>>(Xc, n, nullptr);
+      CKL();
+      TRY(cholqr<double>(ctx, wc, Xc, nc, n, tmp64, 1e-14));
+      TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+      TRY(gram<double>(ctx, wc, Xc, nc, HX64, nc, n, Gc, true));
+      TRY(syev64(ctx, wc, Gc, nc, wcv, Zc));
+      TRY(combine<double>(ctx, Zc, true, nc, nc, Xc, n, tmp64, 1.0, 0.0, nullptr));
+      CK(cudaMemcpyAsync(Xc, tmp64, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
   }
+  TRY(cholqr64_refine(ctx, ws, X64, bf, n, tmp64));
+  TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+  double *Gs, *w, *Zs;
+  TRY(ws.get(&Gs, (size_t)bf * bf));
+  TRY(ws.get(&w, bf));
+  TRY(ws.get(&Zs, (size_t)bf * bf));
+  TRY(gram<double>(ctx, ws, X64, bf, HX64, bf, n, Gs, true));
+  TRY(syev64(ctx, ws, Gs, bf, w, Zs, chunked));
+  double* C = tmp64;
+  TRY(combine<double>(ctx, Zs, true, bf, bf, X64, n, C, 1.0, 0.0, nullptr));
+  std::vector<double> th(bf);
+  TRY(to_host<double>(ctx, w, th.data(), bf));
+  int keff = std::min(k_ret, bf);
+  if (!in.top && k_ret < n) keff = cut_rule(th, keff, ctx->cfg.tau_deg);
   gauge_kernel<<<keff, 256, 0, ctx->stream>>>(C, n);
   CKL();
   const int nc = (int)in.carry.size();
@@ -938,6 +1155,7 @@ rmc_status rmc_create(rmc_ctx** out, const rmc_config* cfg_in) {
   if (cfg.tau_deg <= 0) cfg.tau_deg = 1e-7;
   ctx->cfg = cfg;
   ctx->device = cfg.device;
+  if (const char* t = std::getenv("RMC_TRACE")) ctx->trace = std::atoi(t);
   ctx->budget = cfg.mem_budget;
   CK(cudaSetDevice(ctx->device));
   if (cfg.stream) {

@@ -74,10 +74,16 @@ size_t estimate(const ChainCopy& c, int precision) {
       const double dim = (double)ka * kb;
       const int kr = (int)std::min<double>(top ? q : k, dim);
       const int g = std::max(16, kr / 2);
-      const double b = std::min<double>(std::min<double>(dim, kr + g), 160.0);
+      double b = std::min<double>(dim, kr + g);
+      const bool chunked = b > 160.0 && kr + 1 + 16 > 160 && dim > 160.0;
+      if (chunked) b = std::min<double>(dim, kr + 32);
+      else b = std::min(b, 160.0);
+      const double bw = std::min(b, 160.0);  // working block of the subspace iteration
       const double no = std::max(1, n_ops);
-      double ws = 8.0 * b * dim * (4.0 + no) + 8.0 * dim + 64.0 * 8.0 * b * b * 4.0;
-      if (precision != RMC_PREC_FP64) ws += 4.0 * b * dim * (6.0 + no);
+      double ws = 8.0 * b * dim * (4.0 + no) + 8.0 * 3.0 * std::min(b, 128.0) * dim + 8.0 * dim +
+                  64.0 * 8.0 * b * b * 6.0;
+      if (precision != RMC_PREC_FP64) ws += 4.0 * (2.0 * b + bw * (4.0 + no)) * dim;
+      else ws += 8.0 * bw * (4.0 + no) * dim;
       *peak = std::max(*peak, ws);
       *blocks += 8.0 * (kr + (double)n_ops * kr * kr + dim * kr);
       *kout = kr;

@@ -63,6 +63,16 @@ def test_full_k_tfim_matches_free_fermions(ctx):
     _close(ctx, ctx.solve_chain(c), CF.tfim_lowest(12, 1.0, 0.9, 8))
 
 
+def test_k256_random_field_chain_is_exact(ctx):
+    """Random-field Heisenberg, 16 sites, leaves of 4, k = 256: the first level
+    keeps every state (256 of 256, wider than one Rayleigh-Ritz block, so it is
+    solved chunk by chunk with locking) and the top merge (dimension 65536) is
+    then the exact problem: its lowest energies are the chain's exact ones."""
+    rng = np.random.default_rng(31)
+    c = I.xxz(16, [1.0] * 15, 1.0, 4, 256, 8, fields=list(rng.uniform(-2, 2, 16)))
+    _close(ctx, ctx.solve_chain(c), O.sparse_exact_lowest(c, 8))
+
+
 def test_truncated_energies_are_upper_bounds(ctx):
     c = I.tfim(32, 1.0, 0.7, 4, 16, 4)
     E = ctx.solve_chain(c)

@@ -114,6 +114,40 @@ def test_merge_matches_oracle(ctx, case):
         h.free()
 
 
+LARGE_MERGES = [
+    # kept counts wider than one Rayleigh-Ritz block: solved chunk by chunk with locking
+    (I.xxz(16, list(np.random.default_rng(21).uniform(0.5, 1.5, 15)), 1.0, 8, 50, 8), (0, 8), (8, 16), 220),
+    (I.xxz(16, [1.0] * 15, 1.0, 8, 48, 8, fields=list(np.random.default_rng(22).uniform(-2, 2, 16))),
+     (0, 8), (8, 16), 300),
+]
+
+
+@pytest.mark.parametrize("case", range(len(LARGE_MERGES)))
+def test_wide_merge_with_locking_matches_oracle(ctx, case):
+    chain, Ar, Br, keep = LARGE_MERGES[case]
+    A = O.leaf_block(chain, *Ar, chain.k)
+    B = O.leaf_block(chain, *Br, chain.k)
+    ref, rec = O.merge_blocks(chain, A, B, keep, False)
+    hA, kA_keys = _import(ctx, A)
+    hB, kB_keys = _import(ctx, B)
+    terms = [(c, kA_keys.index(ka), kB_keys.index(kb)) for c, ka, kb in O.merge_terms(chain, *Ar, *Br)]
+    keys = O.boundary_ops(chain, Ar[0], Br[1])
+    carry = [(0, kA_keys.index(k)) if k[0] < Ar[1] else (1, kB_keys.index(k)) for k in keys]
+    blk = ctx.couple(hA, hB, terms, keep, carry)
+    E, ops, basis = blk.export()
+    etol, stol = TOL[ctx.precision]
+    assert len(E) == len(ref.E)
+    np.testing.assert_allclose(E, ref.E, atol=etol * max(1, np.abs(ref.E).max()))
+    sv = overlap_singular_values(ref.U, basis.T)
+    assert sv.min() >= 1 - stol, sv.min()
+    G = ref.U.T @ basis.T
+    for j, key in enumerate(keys):
+        np.testing.assert_allclose(ops[j], G.T @ ref.ops[key] @ G, atol=1e3 * stol)
+    np.testing.assert_allclose(basis @ basis.T, np.eye(len(E)), atol=1e-12)
+    for h in (blk, hA, hB):
+        h.free()
+
+
 def test_zero_coupling_is_sorted_sums(ctx):
     c = I.tfim(8, 1.0, 0.8, 4, 16, 20)
     A = O.leaf_block(c, 0, 4, 16)

@@ -82,6 +82,19 @@ def test_full_k_equals_exact_diagonalisation(chain):
     np.testing.assert_allclose(r.energies, O.exact_spectrum(chain, chain.q), atol=1e-12)
 
 
+@pytest.mark.parametrize("chain", [
+    I.xxz(8, [0.7, 1.1, 0.9, 1.4, 0.6, 1.2, 1.0], 1.0, 8, 4, 6),
+    I.xxz(9, [1.0] * 8, 1.0, 9, 4, 6, fields=[0.5, -1.2, 1.9, 0.1, -0.7, 1.1, -1.8, 0.3, 0.9]),
+])
+def test_sparse_exact_matches_dense(chain):
+    np.testing.assert_allclose(O.sparse_exact_lowest(chain, 6), O.exact_spectrum(chain, 6), atol=1e-11)
+
+
+def test_sparse_exact_16_sites_matches_free_fermions():
+    c = I.tfim(16, 1.0, 0.8, 16, 4, 6)
+    np.testing.assert_allclose(O.sparse_exact_lowest(c, 6), CF.tfim_lowest(16, 1.0, 0.8, 6), atol=1e-10)
+
+
 def test_full_k_tfim_12_sites_equals_free_fermions():
     c = I.tfim(12, 1.0, 0.9, 3, 64, 8)      # leaves of 3 (D = 8), then 64, then 4096: exact
     r = O.solve(c)
