@@ -473,14 +473,19 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
   const bool wide = nv > kMaxSmallDim;  // too wide for the one-CTA factorisation: the block is
                                         // then orthonormal to working precision, first order suffices
   if (!wide) {
-    TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
+    // an FP32 factorisation of the FP64 Gram matrix, and a second one (first
+    // order when the first left it within 1e-3 of the identity) for blocks
+    // conditioned up to ~1e3
     const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
     CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(float))));
-    cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2);
-    CKL();
-    TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
-    CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int pass = 0; pass < 2; ++pass) {
+      TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
+      cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2, pass);
+      CKL();
+      TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
+      CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
   }
   for (int pass = 0; pass < (wide ? 3 : 2); ++pass) {
     TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
@@ -1004,31 +1009,8 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
         TRY((chfsi<W>(ctx, ws, Hw, b, k_conv, idx, ub, tolw, ctx->cfg.max_iter, Xw, HXw, thw, &iters, &converged)));
       convert_kernel<double, W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(Xw, X64, (long)b * n);
       CKL();
-      // FP64 refinement of the working-precision subspace: one FP64 Chebyshev
-      // filter pass over the converged block (same bounds; degree for an
-      // amplification ratio of 1e6, at most 12), which shrinks its residual by
-      // the filter's contraction before the FP64 finalisation.
       th_work.resize(b);
       TRY(to_host<W>(ctx, thw, th_work.data(), b));
-      const std::vector<double>& th32 = th_work;
-      const double a = th32[b - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
-      if (e > 0 && !chunked) {
-        Workspace wp(ctx);
-        double *Y0, *Y1, *Y2, *Yout = nullptr;
-        TRY(wp.get(&Y0, (size_t)b * n));
-        TRY(wp.get(&Y1, (size_t)b * n));
-        TRY(wp.get(&Y2, (size_t)b * n));
-        const double x0 = std::fabs((th32[0] - cc) / e);
-        int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
-        deg = std::max(2, std::min(12, deg));
-        TRY(kron_apply<double>(ctx, H64, X64, b, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
-        TRY((cheb_filter<double>(ctx, H64, X64, HX64, b, th32[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
-        CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        normalize_kernel<double><<<b, 256, 0, ctx->stream>>>(X64, n, nullptr);
-        CKL();
-        // the filtered block can be conditioned up to the filter's ratio: FP64 factorisation
-        TRY(cholqr<double>(ctx, wp, X64, b, n, tmp64, 1e-14));
-      }
     }
   }
   // FP64 finalisation: orthonormalise, project, refined small eigensolve, on
@@ -1077,16 +1059,60 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
       CK(cudaMemcpyAsync(Xc, tmp64, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
     }
   }
-  TRY(cholqr64_refine(ctx, ws, X64, bf, n, tmp64));
-  TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
-  double *Gs, *w, *Zs;
+  // Mixed paths (single block): FP64 refinement of the working-precision
+  // subspace, repeated until the FP64 residuals of the wanted vectors are below
+  // kRefineTol relative (at most kRefinePasses passes).  A pass is one FP64
+  // Chebyshev filter pass over the block (bounds from the current Ritz values;
+  // degree for an amplification ratio of 1e3, at most 8, so the filtered
+  // block stays within reach of an FP32 Cholesky factorisation), the FP64
+  // Cholesky-QR, and the FP64 Rayleigh-Ritz of the finalisation.
+  constexpr int kRefinePasses = 4;
+  constexpr double kRefineTol = 1e-8;
+  const bool refine = sizeof(W) == 4 && !chunked && !dense && th_work.size() == (size_t)bf;
+  std::vector<double> th_cur = th_work;
+  double *Gs, *w, *Zs, *rn64;
   TRY(ws.get(&Gs, (size_t)bf * bf));
   TRY(ws.get(&w, bf));
   TRY(ws.get(&Zs, (size_t)bf * bf));
-  TRY(gram<double>(ctx, ws, X64, bf, HX64, bf, n, Gs, true));
-  TRY(syev64(ctx, ws, Gs, bf, w, Zs, chunked));
+  TRY(ws.get(&rn64, bf));
   double* C = tmp64;
-  TRY(combine<double>(ctx, Zs, true, bf, bf, X64, n, C, 1.0, 0.0, nullptr));
+  for (int pass = 0;; ++pass) {
+    if (refine) {
+      const double a = th_cur[bf - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
+      if (e > 0) {
+        Workspace wp(ctx);
+        double *Y0, *Y1, *Y2, *Yout = nullptr;
+        TRY(wp.get(&Y0, (size_t)bf * n));
+        TRY(wp.get(&Y1, (size_t)bf * n));
+        TRY(wp.get(&Y2, (size_t)bf * n));
+        const double x0 = std::fabs((th_cur[0] - cc) / e);
+        int deg = (int)std::floor(std::acosh(1e3) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+        deg = std::max(2, std::min(8, deg));
+        TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+        TRY((cheb_filter<double>(ctx, H64, X64, HX64, bf, th_cur[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
+        CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        normalize_kernel<double><<<bf, 256, 0, ctx->stream>>>(X64, n, nullptr);
+        CKL();
+      }
+    }
+    TRY(cholqr64_refine(ctx, ws, X64, bf, n, tmp64));
+    TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+    TRY(gram<double>(ctx, ws, X64, bf, HX64, bf, n, Gs, true));
+    TRY(syev64(ctx, ws, Gs, bf, w, Zs, chunked));
+    TRY(combine<double>(ctx, Zs, true, bf, bf, X64, n, C, 1.0, 0.0, nullptr));
+    if (!refine || pass + 1 >= kRefinePasses) break;
+    // FP64 residuals of the Ritz vectors (H C = Z^T H X)
+    double* HC = Tb64;
+    TRY(combine<double>(ctx, Zs, true, bf, bf, HX64, n, HC, 1.0, 0.0, nullptr));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    residual_kernel<double><<<bf, 256, 0, ctx->stream>>>(C, HC, w, n, k_conv, kRefineTol, rn64, ctx->d_status);
+    CKL();
+    int fails = 0;
+    TRY(read_status(ctx, &fails, 1));
+    if (fails == 0) break;
+    TRY(to_host<double>(ctx, w, th_cur.data(), bf));
+    CK(cudaMemcpyAsync(X64, C, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
   std::vector<double> th(bf);
   TRY(to_host<double>(ctx, w, th.data(), bf));
   int keff = std::min(k_ret, bf);
