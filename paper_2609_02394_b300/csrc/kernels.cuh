@@ -263,6 +263,32 @@ __global__ void __launch_bounds__(1024) select_smallest_kernel(const double* __r
   for (int i = tid; i < b; i += blockDim.x) idx[i] = sidx[i];
 }
 
+// Start block of the subspace iteration: X[i] = e_{idx[i]} + amp * r_i, r_i
+// uniform in [-1, 1) per element from the splitmix64 mixing function (Steele,
+// Lea and Flood, 2014) of the element's flat index.  The unit vectors alone
+// each lie in one symmetry sector of H (parity, magnetisation) and the filter
+// keeps them there, so a low state whose sector holds too few of the chosen
+// unit vectors would never enter the block; the small deterministic
+// perturbation gives every vector a component in every sector.  Writes all of
+// X (vector-major, b x n).
+__device__ __forceinline__ double splitmix_uniform(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+template <typename T>
+__global__ void start_vectors_kernel(const int* __restrict__ idx, int b, long n, double amp, T* __restrict__ X) {
+  const long total = (long)b * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n);
+    const long r = e - (long)i * n;
+    X[e] = T((r == idx[i] ? 1.0 : 0.0) + amp * splitmix_uniform((unsigned long long)e));
+  }
+}
+
 // X[i] = e_{idx[i]}  (vector-major, X zeroed by the caller)
 template <typename T>
 __global__ void unit_vectors_kernel(const int* __restrict__ idx, int b, long n, T* __restrict__ X) {

@@ -634,13 +634,25 @@ struct MergeInput {
   bool top;
 };
 
+template <typename W>
+rmc_status project_out(rmc_ctx* ctx, const W* Xl, int nl, W* Xa, int na, long n, W* C, int passes = 2);
+
 // Chebyshev filter (Zhou and Saad's scaled three-term recurrence) of degree
 // deg >= 2 applied to the block X with H X given: damps [a, ub], scaled at
 // theta0.  Uses Y0, Y1, Y2 (b x n each) and leaves the result in *out (one of
 // them); X and HX are left unchanged.
+//
+// With nl > 0 locked vectors Ql (orthonormal, below theta0) the filter runs on
+// the deflated operator P H P, P = I - Ql^T Ql: each new term has the locked
+// span removed (one Gram-Schmidt pass, Cbuf holds nl x b coefficients).  The
+// polynomial is largest below the damped interval, so without this the
+// rounding-level locked components of X would grow by T_deg at the locked
+// eigenvalues, far faster than the wanted ones, and swamp them in working
+// precision.
 template <typename W>
 rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX, int b, double theta0, double a,
-                       double ub, int deg, W* Y0, W* Y1, W* Y2, W* Tbuf, W** out) {
+                       double ub, int deg, W* Y0, W* Y1, W* Y2, W* Tbuf, W** out, const W* Ql = nullptr,
+                       int nl = 0, W* Cbuf = nullptr) {
   const long n = H.n();
   const double e = (ub - a) / 2, c = (ub + a) / 2;
   double sigma = e / (theta0 - c);
@@ -649,6 +661,7 @@ rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX
   axpby_kernel<W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(HX, X, (long)b * n, W(sigma / e),
                                                                  W(-c * sigma / e), Y1);
   CKL();
+  TRY(project_out<W>(ctx, Ql, nl, Y1, b, n, Cbuf, 1));
   const W* Yprev = X;
   W* Ycur = Y1;
   W* Ynext = Y2;
@@ -656,6 +669,7 @@ rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX
   for (int d = 2; d <= deg; ++d) {
     const double s1 = 1.0 / (tau - sigma);
     TRY(kron_work<W>(ctx, H, Ycur, b, Ynext, W(2 * s1 / e), W(-2 * s1 * c / e), W(-sigma * s1), Yprev, Tbuf));
+    TRY(project_out<W>(ctx, Ql, nl, Ynext, b, n, Cbuf, 1));
     // rotate: the buffer two steps back is free unless it is X itself
     W* old_prev = const_cast<W*>(Yprev);
     Yprev = Ycur;
@@ -665,6 +679,42 @@ rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX
   }
   *out = Ycur;
   return RMC_OK;
+}
+
+// Norm of the pseudo-random part of each start vector (per element amplitude
+// kStartAmp / sqrt(n), uniform, so the norm is about kStartAmp / sqrt(3)).
+constexpr double kStartAmp = 1e-2;
+
+// Rounding floor of the FP32 iterations (mixed paths): the worst relative
+// residual of the wanted vectors has not halved in kStallIters iterations and
+// is within kStallFactor of the tolerance.  The iteration then stops as
+// converged and the FP64 refinement that follows sets the final accuracy (its
+// own residual test decides).  Wide blocks of large merges reach a floor of a
+// few 1e-6 relative in FP32.
+constexpr int kStallIters = 8;
+constexpr double kStallFactor = 20.0;
+struct StallGuard {
+  double best = 1e300;
+  int since = 0;
+  bool at_floor(double worst, double tol) {
+    if (worst < 0.5 * best) {
+      best = worst;
+      since = 0;
+      return false;
+    }
+    return ++since >= kStallIters && worst < kStallFactor * tol;
+  }
+};
+
+// Worst relative residual r_i / max(1, |theta_i|) over the first m vectors.
+inline double worst_relative(const std::vector<double>& r, const std::vector<double>& th, int m, int* at) {
+  double w = 0;
+  *at = 0;
+  for (int i = 0; i < m; ++i) {
+    const double v = r[i] / std::max(1.0, std::fabs(th[i]));
+    if (v > w) { w = v; *at = i; }
+  }
+  return w;
 }
 
 template <typename W>
@@ -685,8 +735,7 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
   const double rho = fp64 ? 1e6 : 1e3;  // cap on the filter's amplification ratio
   const int dmax = 40;
 
-  CK(cudaMemsetAsync(X, 0, sizeof(W) * b * n, ctx->stream));
-  unit_vectors_kernel<W><<<ceil_div(b, 128), 128, 0, ctx->stream>>>(d_idx, b, n, X);
+  start_vectors_kernel<W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(d_idx, b, n, kStartAmp / std::sqrt((double)n), X);
   CKL();
   auto rayleigh_ritz = [&]() -> rmc_status {
     Workspace wl(ctx);
@@ -710,23 +759,25 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
   W* X_orig = X;
   W* HX_orig = HX;
   TRY(rayleigh_ritz());
-  std::vector<double> th(b);
+  std::vector<double> th(b), r(b);
+  StallGuard stall;
   int it = 0;
   *converged = false;
   for (;; ++it) {
     int fails = 0;
     TRY(read_status(ctx, &fails, 1));
     TRY(to_host<W>(ctx, theta, th.data(), b));
-    if (ctx->trace) {
-      std::vector<double> r(b);
+    double worst = 0;
+    int wi = 0;
+    if (ctx->trace || (!fp64 && fails > 0)) {
       TRY(to_host<double>(ctx, rn, r.data(), b));
-      int worst = 0;
-      for (int i = 0; i < k_conv; ++i)
-        if (r[i] / std::max(1.0, std::fabs(th[i])) > r[worst] / std::max(1.0, std::fabs(th[worst]))) worst = i;
-      fprintf(stderr, "[rmc] n=%ld b=%d it=%d fails=%d worst i=%d res=%.3e theta=%.12g th0=%.12g thb=%.12g\n", n, b, it,
-              fails, worst, r[worst] / std::max(1.0, std::fabs(th[worst])), th[worst], th[0], th[b - 1]);
+      worst = worst_relative(r, th, k_conv, &wi);
     }
+    if (ctx->trace)
+      fprintf(stderr, "[rmc] n=%ld b=%d it=%d fails=%d worst i=%d res=%.3e theta=%.12g th0=%.12g thb=%.12g\n", n, b, it,
+              fails, wi, worst, th[wi], th[0], th[b - 1]);
     if (fails == 0) { *converged = true; break; }
+    if (!fp64 && stall.at_floor(worst, tol)) { *converged = true; break; }
     if (it >= max_iter) break;
     ctx->iterations++;
     const double a = th[b - 1];
@@ -756,12 +807,13 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
 }
 
 
-// X_a <- X_a - X_l^T (X_l X_a^T)^T, twice: remove the span of the nl locked
-// vectors X_l from the na vectors X_a (classical Gram-Schmidt, two passes).
+// X_a <- X_a - X_l^T (X_l X_a^T)^T, `passes` times: remove the span of the nl
+// locked vectors X_l from the na vectors X_a (classical Gram-Schmidt; two
+// passes unless the caller repeats it anyway).
 template <typename W>
-rmc_status project_out(rmc_ctx* ctx, const W* Xl, int nl, W* Xa, int na, long n, W* C) {
+rmc_status project_out(rmc_ctx* ctx, const W* Xl, int nl, W* Xa, int na, long n, W* C, int passes) {
   if (nl <= 0) return RMC_OK;
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     Workspace wl(ctx);
     TRY(gram<W>(ctx, wl, Xl, nl, Xa, na, n, C, false));   // C[i][j] = <x_l_i, x_a_j>
     TRY(combine<W>(ctx, C, true, na, nl, Xl, n, Xa, W(-1), W(1), Xa));
@@ -797,8 +849,8 @@ rmc_status chfsi_locked(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b_t
   const bool fp64 = sizeof(W) == 8;
   const double rho = fp64 ? 1e6 : 1e3;
   const int dmax = 40;
-  CK(cudaMemsetAsync(X, 0, sizeof(W) * b_total * n, ctx->stream));
-  unit_vectors_kernel<W><<<ceil_div(b_total, 128), 128, 0, ctx->stream>>>(d_idx, b_total, n, X);
+  start_vectors_kernel<W><<<grid1d((long)b_total * n), 256, 0, ctx->stream>>>(d_idx, b_total, n,
+                                                                               kStartAmp / std::sqrt((double)n), X);
   CKL();
   *converged = true;
   int total_it = 0;
@@ -835,21 +887,23 @@ rmc_status chfsi_locked(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b_t
     };
     TRY(orthonormalise());
     TRY(rayleigh_ritz());
-    std::vector<double> th(ba);
+    std::vector<double> th(ba), r(ba);
+    StallGuard stall;
     for (int it = 0;; ++it) {
       int fails = 0;
       TRY(read_status(ctx, &fails, 1));
       TRY(to_host<W>(ctx, tha, th.data(), ba));
-      if (ctx->trace) {
-        std::vector<double> r(ba);
+      double worst = 0;
+      int wi = 0;
+      if (ctx->trace || (!fp64 && fails > 0)) {
         TRY(to_host<double>(ctx, rn, r.data(), ba));
-        int worst = 0;
-        for (int i = 0; i < c; ++i)
-          if (r[i] / std::max(1.0, std::fabs(th[i])) > r[worst] / std::max(1.0, std::fabs(th[worst]))) worst = i;
-        fprintf(stderr, "[rmc locked] n=%ld L=%d c=%d ba=%d it=%d fails=%d worst i=%d res=%.3e theta=%.12g\n", n, L, c,
-                ba, it, fails, worst, r[worst] / std::max(1.0, std::fabs(th[worst])), th[worst]);
+        worst = worst_relative(r, th, c, &wi);
       }
+      if (ctx->trace)
+        fprintf(stderr, "[rmc locked] n=%ld L=%d c=%d ba=%d it=%d fails=%d worst i=%d res=%.3e theta=%.12g\n", n, L, c,
+                ba, it, fails, wi, worst, th[wi]);
       if (fails == 0) break;
+      if (!fp64 && stall.at_floor(worst, tol)) break;
       if (it >= max_iter) { *converged = false; break; }
       ctx->iterations++;
       total_it++;
@@ -860,7 +914,7 @@ rmc_status chfsi_locked(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b_t
       int deg = (int)std::floor(std::acosh(rho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
       deg = std::max(2, std::min(dmax, deg));
       W* Yout = nullptr;
-      TRY((cheb_filter<W>(ctx, H, Xa, HXa, ba, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout)));
+      TRY((cheb_filter<W>(ctx, H, Xa, HXa, ba, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout, X, L, C)));
       CK(cudaMemcpyAsync(Xa, Yout, sizeof(W) * ba * n, cudaMemcpyDeviceToDevice, ctx->stream));
       TRY(orthonormalise());
       TRY(rayleigh_ritz());
@@ -1016,59 +1070,24 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   // FP64 finalisation: orthonormalise, project, refined small eigensolve, on
   // the whole block (the guard vectors improve the Rayleigh-Ritz extraction of
   // the wanted subspace: restricting it to the wanted vectors cost accuracy).
+  //
+  // Mixed paths: FP64 refinement of the working-precision subspace, repeated
+  // until the FP64 residuals of the wanted vectors are below kRefineTol
+  // relative (at most kRefinePasses passes).  A pass is one FP64 Chebyshev
+  // filter pass (bounds from the current Ritz values), the FP64 Cholesky-QR
+  // and the FP64 Rayleigh-Ritz.  A single block is filtered whole, with the
+  // degree for an amplification ratio of 1e3 (at most 8) so the filtered block
+  // stays within reach of the FP32 Cholesky factorisation that starts
+  // cholqr64_refine.  A locked block is filtered chunk by chunk (at most 128
+  // vectors, degree for 1e6, at most 12) on the operator deflated by the
+  // earlier chunks, and each chunk is orthonormalised against them and
+  // rotated to its own Ritz vectors, so the global Rayleigh-Ritz is nearly
+  // diagonal and its eigensolver starts from the identity.  The FP64 path of
+  // a locked block takes the chunk orthonormalisation once, without filter.
   const int bf = b;
-  if (chunked) {
-    // Chunk by chunk (at most 128 vectors each): the FP64 filter pass of the
-    // mixed paths, removal of the earlier chunks' span, FP64 Cholesky-QR and a
-    // chunk Rayleigh-Ritz.  The global Rayleigh-Ritz below is then nearly
-    // diagonal and its refinement starts from the identity.
-    const int cw = 128;
-    Workspace wc(ctx);
-    double *Y0, *Y1, *Y2, *Cp, *Gc, *Zc, *wcv;
-    TRY(wc.get(&Y0, (size_t)cw * n));
-    TRY(wc.get(&Y1, (size_t)cw * n));
-    TRY(wc.get(&Y2, (size_t)cw * n));
-    TRY(wc.get(&Cp, (size_t)bf * cw));
-    TRY(wc.get(&Gc, (size_t)cw * cw));
-    TRY(wc.get(&Zc, (size_t)cw * cw));
-    TRY(wc.get(&wcv, cw));
-    const bool polish = sizeof(W) == 4 && th_work.size() == (size_t)bf;
-    for (int s0 = 0; s0 < bf; s0 += cw) {
-      const int nc = std::min(cw, bf - s0);
-      double* Xc = X64 + (size_t)s0 * n;
-      if (polish && nc >= 2) {
-        const double a = th_work[s0 + nc - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
-        if (e > 0) {
-          const double x0 = std::fabs((th_work[s0] - cc) / e);
-          int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
-          deg = std::max(2, std::min(12, deg));
-          double* Yout = nullptr;
-          TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
-          TRY((cheb_filter<double>(ctx, H64, Xc, HX64, nc, th_work[s0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
-          CK(cudaMemcpyAsync(Xc, Yout, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        }
-      }
-      TRY(project_out<double>(ctx, X64, s0, Xc, nc, n, Cp));
-      normalize_kernel<double><<<nc, 256, 0, ctx->stream>>>(Xc, n, nullptr);
-      CKL();
-      TRY(cholqr<double>(ctx, wc, Xc, nc, n, tmp64, 1e-14));
-      TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
-      TRY(gram<double>(ctx, wc, Xc, nc, HX64, nc, n, Gc, true));
-      TRY(syev64(ctx, wc, Gc, nc, wcv, Zc));
-      TRY(combine<double>(ctx, Zc, true, nc, nc, Xc, n, tmp64, 1.0, 0.0, nullptr));
-      CK(cudaMemcpyAsync(Xc, tmp64, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-  }
-  // Mixed paths (single block): FP64 refinement of the working-precision
-  // subspace, repeated until the FP64 residuals of the wanted vectors are below
-  // kRefineTol relative (at most kRefinePasses passes).  A pass is one FP64
-  // Chebyshev filter pass over the block (bounds from the current Ritz values;
-  // degree for an amplification ratio of 1e3, at most 8, so the filtered
-  // block stays within reach of an FP32 Cholesky factorisation), the FP64
-  // Cholesky-QR, and the FP64 Rayleigh-Ritz of the finalisation.
   constexpr int kRefinePasses = 4;
   constexpr double kRefineTol = 1e-8;
-  const bool refine = sizeof(W) == 4 && !chunked && !dense && th_work.size() == (size_t)bf;
+  const bool refine = sizeof(W) == 4 && !dense && th_work.size() == (size_t)bf;
   std::vector<double> th_cur = th_work;
   double *Gs, *w, *Zs, *rn64;
   TRY(ws.get(&Gs, (size_t)bf * bf));
@@ -1077,7 +1096,46 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   TRY(ws.get(&rn64, bf));
   double* C = tmp64;
   for (int pass = 0;; ++pass) {
-    if (refine) {
+    if (chunked) {
+      const int cw = 128;
+      Workspace wc(ctx);
+      double *Y0, *Y1, *Y2, *Cp, *Gc, *Zc, *wcv;
+      TRY(wc.get(&Y0, (size_t)cw * n));
+      TRY(wc.get(&Y1, (size_t)cw * n));
+      TRY(wc.get(&Y2, (size_t)cw * n));
+      TRY(wc.get(&Cp, (size_t)bf * cw));
+      TRY(wc.get(&Gc, (size_t)cw * cw));
+      TRY(wc.get(&Zc, (size_t)cw * cw));
+      TRY(wc.get(&wcv, cw));
+      for (int s0 = 0; s0 < bf; s0 += cw) {
+        const int nc = std::min(cw, bf - s0);
+        double* Xc = X64 + (size_t)s0 * n;
+        if (refine && nc >= 2) {
+          const double a = th_cur[s0 + nc - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
+          if (e > 0) {
+            const double x0 = std::fabs((th_cur[s0] - cc) / e);
+            int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+            deg = std::max(2, std::min(12, deg));
+            double* Yout = nullptr;
+            TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+            TRY((cheb_filter<double>(ctx, H64, Xc, HX64, nc, th_cur[s0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout, X64,
+                                     s0, Cp)));
+            CK(cudaMemcpyAsync(Xc, Yout, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
+          }
+        }
+        if (refine || pass == 0) {
+          TRY(project_out<double>(ctx, X64, s0, Xc, nc, n, Cp));
+          normalize_kernel<double><<<nc, 256, 0, ctx->stream>>>(Xc, n, nullptr);
+          CKL();
+          TRY(cholqr<double>(ctx, wc, Xc, nc, n, tmp64, 1e-14));
+          TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+          TRY(gram<double>(ctx, wc, Xc, nc, HX64, nc, n, Gc, true));
+          TRY(syev64(ctx, wc, Gc, nc, wcv, Zc));
+          TRY(combine<double>(ctx, Zc, true, nc, nc, Xc, n, tmp64, 1.0, 0.0, nullptr));
+          CK(cudaMemcpyAsync(Xc, tmp64, sizeof(double) * nc * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+      }
+    } else if (refine) {
       const double a = th_cur[bf - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
       if (e > 0) {
         Workspace wp(ctx);
@@ -1109,6 +1167,7 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
     CKL();
     int fails = 0;
     TRY(read_status(ctx, &fails, 1));
+    if (ctx->trace) fprintf(stderr, "[rmc refine] n=%ld b=%d pass=%d fails=%d\n", n, bf, pass, fails);
     if (fails == 0) break;
     TRY(to_host<double>(ctx, w, th_cur.data(), bf));
     CK(cudaMemcpyAsync(X64, C, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));

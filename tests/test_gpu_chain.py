@@ -77,3 +77,18 @@ def test_truncated_energies_are_upper_bounds(ctx):
     c = I.tfim(32, 1.0, 0.7, 4, 16, 4)
     E = ctx.solve_chain(c)
     assert np.all(E >= CF.tfim_lowest(32, 1.0, 0.7, 4) - 1e-9)
+
+
+def test_degenerate_k256_chain_mixed_agrees_with_fp64():
+    """A 50-site Heisenberg chain (random couplings, SU(2) multiplets) with
+    k = 256 from the serving mix: every merge keeps 256 of up to 65536 states,
+    so each is solved chunk by chunk with a one-vector tail chunk above 256
+    locked vectors.  The mixed path must converge and agree with the FP64 path
+    (no oracle: the merges are too wide for dense FP64 on the host)."""
+    torch_cuda()
+    c = I.serving_requests(48, seed=I.seed_for(5))[45]
+    assert (c.n_sites, c.k) == (50, 256)
+    with P.Context(precision="fp64") as c64, P.Context(precision="mixed") as cm:
+        ref = c64.solve_chain(c)
+        got = cm.solve_chain(c)
+    assert np.all(np.abs(got - ref) <= 1e-8 * np.maximum(1.0, np.abs(ref))), got - ref

@@ -119,6 +119,9 @@ LARGE_MERGES = [
     (I.xxz(16, list(np.random.default_rng(21).uniform(0.5, 1.5, 15)), 1.0, 8, 50, 8), (0, 8), (8, 16), 220),
     (I.xxz(16, [1.0] * 15, 1.0, 8, 48, 8, fields=list(np.random.default_rng(22).uniform(-2, 2, 16))),
      (0, 8), (8, 16), 300),
+    # 256 kept from 64 x 64: two full chunks and a one-vector tail chunk right
+    # above 256 locked vectors (the filter must not amplify the locked span)
+    (I.xxz(16, list(np.random.default_rng(23).uniform(0.5, 1.5, 15)), 1.0, 8, 64, 8), (0, 8), (8, 16), 256),
 ]
 
 
