@@ -473,15 +473,15 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
   const bool wide = nv > kMaxSmallDim;  // too wide for the one-CTA factorisation: the block is
                                         // then orthonormal to working precision, first order suffices
   if (!wide) {
-    // an FP32 factorisation of the FP64 Gram matrix, and a second one (first
-    // order when the first left it within 1e-3 of the identity) for blocks
-    // conditioned up to ~1e3
-    const size_t sm = cholinv_smem_bytes(nv, sizeof(float));
-    CK(cudaFuncSetAttribute(cholinv_kernel<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(float))));
+    // an FP64 factorisation of the Gram matrix, and a second one (first order
+    // when the first left it within 1e-3 of the identity): blocks conditioned
+    // up to ~1e6, as left by the refinement filter, come out orthonormal
+    const size_t sm = cholinv_smem_bytes(nv, sizeof(double));
+    CK(cudaFuncSetAttribute(cholinv_kernel<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(double))));
     for (int pass = 0; pass < 2; ++pass) {
       TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
-      cholinv_kernel<float, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2, pass);
+      cholinv_kernel<double, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2, pass);
       CKL();
       TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
       CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1076,9 +1076,10 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   // relative (at most kRefinePasses passes).  A pass is one FP64 Chebyshev
   // filter pass (bounds from the current Ritz values), the FP64 Cholesky-QR
   // and the FP64 Rayleigh-Ritz.  A single block is filtered whole, with the
-  // degree for an amplification ratio of 1e3 (at most 8) so the filtered block
-  // stays within reach of the FP32 Cholesky factorisation that starts
-  // cholqr64_refine.  A locked block is filtered chunk by chunk (at most 128
+  // degree for an amplification ratio of 1e6 (at most 16): the wanted vectors
+  // nearest the guard then gain ~1e3 over the damped interval in one pass,
+  // and the FP64 factorisation of cholqr64_refine absorbs the conditioning
+  // this leaves in the guard columns.  A locked block is filtered chunk by chunk (at most 128
   // vectors, degree for 1e6, at most 12) on the operator deflated by the
   // earlier chunks, and each chunk is orthonormalised against them and
   // rotated to its own Ritz vectors, so the global Rayleigh-Ritz is nearly
@@ -1144,8 +1145,8 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
         TRY(wp.get(&Y1, (size_t)bf * n));
         TRY(wp.get(&Y2, (size_t)bf * n));
         const double x0 = std::fabs((th_cur[0] - cc) / e);
-        int deg = (int)std::floor(std::acosh(1e3) / std::acosh(std::max(x0, 1.0 + 1e-12)));
-        deg = std::max(2, std::min(8, deg));
+        int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+        deg = std::max(2, std::min(16, deg));
         TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
         TRY((cheb_filter<double>(ctx, H64, X64, HX64, bf, th_cur[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
         CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1163,11 +1164,23 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
     double* HC = Tb64;
     TRY(combine<double>(ctx, Zs, true, bf, bf, HX64, n, HC, 1.0, 0.0, nullptr));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-    residual_kernel<double><<<bf, 256, 0, ctx->stream>>>(C, HC, w, n, k_conv, kRefineTol, rn64, ctx->d_status);
+    // only the kept vectors need the FP64 accuracy; the extra one beyond them
+    // serves the cut rule, whose gap test needs its Ritz value only, and that
+    // is accurate to the square of its residual
+    const int k_acc = std::min(k_conv, k_ret);
+    residual_kernel<double><<<bf, 256, 0, ctx->stream>>>(C, HC, w, n, k_acc, kRefineTol, rn64, ctx->d_status);
     CKL();
     int fails = 0;
     TRY(read_status(ctx, &fails, 1));
-    if (ctx->trace) fprintf(stderr, "[rmc refine] n=%ld b=%d pass=%d fails=%d\n", n, bf, pass, fails);
+    if (ctx->trace) {
+      std::vector<double> r(bf), t(bf);
+      TRY(to_host<double>(ctx, rn64, r.data(), bf));
+      TRY(to_host<double>(ctx, w, t.data(), bf));
+      int wi = 0;
+      const double worst = worst_relative(r, t, k_acc, &wi);
+      fprintf(stderr, "[rmc refine] n=%ld b=%d k_conv=%d pass=%d fails=%d worst i=%d res=%.3e theta=%.12g thb=%.12g\n",
+              n, bf, k_conv, pass, fails, wi, worst, t[wi], t[bf - 1]);
+    }
     if (fails == 0) break;
     TRY(to_host<double>(ctx, w, th_cur.data(), bf));
     CK(cudaMemcpyAsync(X64, C, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));
