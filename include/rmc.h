@@ -302,6 +302,24 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
                            const double* coef, const void* X, void* Y, const void* Z,
                            double alpha, double beta, double gamma);
 
+/* The Chebyshev filter of one subspace iteration (Zhou and Saad's scaled
+ * three-term recurrence on the H_eff of Eq. (7), the operator arguments as in
+ * rmc_kron_matvec with dtype 0 = FP64 or 1 = FP32):
+ *   Y[v] = p(H) X[v] / ||p(H) X[v]||,   p = T_deg((H - c) / e) / T_deg((theta0 - c) / e),
+ * e = (ub - a) / 2, c = (ub + a) / 2: the polynomial damps [a, ub] (bounded by
+ * 1 / |T_deg((theta0 - c) / e)| there) and grows below a; theta0 < a < ub
+ * (else RMC_ERR_INVAL), 1 <= deg <= 64.  With deg = 0 it is the plain product
+ * Y = H X (not normalised; theta0, a, ub unused).  fused = 1 runs the
+ * single-launch form that holds the vectors in shared memory for the whole
+ * polynomial (RMC_ERR_INVAL when one k_A x k_B vector with its intermediates
+ * does not fit); fused = 0 runs the multi-launch form (two GEMM launches per
+ * degree).  Y may alias X.  Device pointers; runs on the context stream; does
+ * not synchronise. */
+rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv,
+                           const void* EA, const void* EB, const void* A, const void* B,
+                           const double* coef, const void* X, int deg, double theta0, double a,
+                           double ub, int fused, void* Y);
+
 /* Allocation-free variant of rmc_kron_matvec, for callers that cannot call
  * cudaMalloc: a plug-in running inside a host application that reserved the
  * device memory for its own allocator, or a latency-critical loop that must

@@ -29,7 +29,7 @@ EXPORTED = [
     "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
     "rmc_kron_matvec_noalloc", "rmc_server_create", "rmc_server_destroy", "rmc_submit", "rmc_poll",
     "rmc_server_stats", "rmc_estimate_bytes", "rmc_solve_chains", "rmc_server_profile",
-    "rmc_server_profile_read", "rmc_server_last_error",
+    "rmc_server_profile_read", "rmc_server_last_error", "rmc_cheb_filter",
 ]
 PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_solve_chains": ([P(rmc_config), ip, ip, P(rmc_chain), ip, P(dp), P(ip)], ip),
         "rmc_kron_matvec_noalloc": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
         "rmc_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
+        "rmc_cheb_filter": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, ip, dp, dp, dp, ip, vp], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -340,6 +341,12 @@ class Context:
         c = _f64(coef if len(coef) else [0.0])
         self._check(self.lib.rmc_kron_matvec(self.h, dtype, kA, kB, n_ops, nv, EA, EB, A or None, B or None,
                                              _dptr(c), X, Y, Z or None, alpha, beta, gamma))
+
+    def cheb_filter(self, dtype: int, kA: int, kB: int, n_ops: int, nv: int, EA: int, EB: int, A: int, B: int,
+                    coef, X: int, deg: int, theta0: float, a: float, ub: float, fused: bool, Y: int):
+        c = _f64(coef if len(coef) else [0.0])
+        self._check(self.lib.rmc_cheb_filter(self.h, dtype, kA, kB, n_ops, nv, EA, EB, A or None, B or None,
+                                             _dptr(c), X, deg, theta0, a, ub, 1 if fused else 0, Y))
 
     def syev(self, m: int, S: int, w: int, V: int):
         self._check(self.lib.rmc_syev(self.h, m, S, w, V))

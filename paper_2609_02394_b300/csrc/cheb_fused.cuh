@@ -1,0 +1,201 @@
+// Fused Kronecker-form products with H_eff (Eq. (7)) for blocks whose vectors
+// fit in shared memory: the whole Chebyshev filter of one subspace iteration
+// (Zhou and Saad's scaled three-term recurrence), or one plain product H X,
+// in a single launch.
+//
+// Each vector of the block is a kA x kB matrix and every step of the filter
+// acts on the vectors independently, so a CTA owns `vpc` vectors for the
+// whole polynomial: the two most recent terms of the recurrence and the
+// stage-1 intermediate stay in shared memory, the operators are staged there
+// once (FP32) or read through L1/L2 (FP64), and only the input block and the
+// normalised result cross HBM.  The multi-launch form (two GEMM launches per
+// degree, each term written to and read back from HBM) remains for blocks
+// that do not fit and for the deflated filter of the locked iteration.
+//
+// Per vector v and step, with Y the current term:
+//   stage 1: T[(j, a), (v, b)] = sum_b' Y[v][a][b'] B_j[b][b']
+//   stage 2: (H Y)[v][a][b]    = (EA[a] + EB[b]) Y[v][a][b] + sum_{j,a'} Acat[a][(j,a')] T[(j,a'), (v,b)]
+// where Acat folds the coupling coefficients into the A-side operators.
+#pragma once
+
+#include "common.cuh"
+
+namespace rmc {
+
+constexpr int kFusedThreads = 256;                // 16 x 16 threads, 4 x 4 outputs each per 64 x 64 tile
+constexpr size_t kFusedSmemLimit = 200u * 1024u;  // dynamic shared memory of one CTA
+
+struct FusedArgs {
+  int kA, kB, n_ops, nv;  // block of nv vectors of length kA * kB
+  int vpc;                // vectors per CTA
+  int deg;                // polynomial degree (>= 1) of the filter; 0: plain product
+  int compute_hx;         // 1: H X is formed in the kernel, HX is not read
+  int ops_in_smem;        // operators staged in shared memory
+  double e, c, sigma1;    // filter: half width and centre of the damped interval, e / (theta0 - c)
+};
+
+// C(m, n) = sum_k A(m, k) B(k, n) for an M x N output, A(m, k) = A[m*sam + k*sak],
+// B(k, n) = B[k*sbk + n*sbn], by all threads of the CTA (16 x 16 thread grid,
+// 4 x 4 register tile per thread per 64 x 64 output tile).  Out-of-range rows
+// and columns read a clamped in-range element and are not stored.
+template <typename T, class Epi>
+__device__ __forceinline__ void cta_gemm(int M, int N, int K, const T* A, int sam, int sak, const T* B, int sbk,
+                                         int sbn, const Epi& epi) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int m0 = 0; m0 < M; m0 += 64) {
+    for (int n0 = 0; n0 < N; n0 += 64) {
+      int ar[4], bc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ar[i] = min(m0 + ty + 16 * i, M - 1) * sam;
+        bc[i] = min(n0 + tx + 16 * i, N - 1) * sbn;
+      }
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      for (int k = 0; k < K; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = A[ar[i] + k * sak];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = B[k * sbk + bc[j]];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n = n0 + tx + 16 * j;
+          if (n < N) epi(m, n, acc[i][j]);
+        }
+      }
+    }
+  }
+}
+
+// Stage-1 epilogue: T[((j*kA + a)*nvl + v)*kB + b] for m = v*kA + a, n = j*kB + b.
+template <typename T>
+struct FusedEpi1 {
+  T* Ts;
+  int kA, kB, nvl;
+  __device__ void operator()(int m, int n, T acc) const {
+    const int v = m / kA, a = m - v * kA, j = n / kB, b = n - j * kB;
+    Ts[((j * kA + a) * nvl + v) * kB + b] = acc;
+  }
+};
+
+// Stage-2 epilogue of a recurrence step: with x = Ycur and z = Yold at the
+// same element, Yold <- alpha * (acc + (EA[a] + EB[b]) x) + beta * x + gamma * z
+// (the new term overwrites the one two steps back; gamma = 0 ignores z).
+template <typename T>
+struct FusedEpi2 {
+  const T* Ycur;
+  T* Yold;
+  const T* EA;
+  const T* EB;
+  int kA, kB;
+  T alpha, beta, gamma;
+  __device__ void operator()(int a, int n, T acc) const {
+    const int v = n / kB, b = n - v * kB;
+    const int idx = (v * kA + a) * kB + b;
+    const T x = Ycur[idx];
+    T y = alpha * (acc + (EA[a] + EB[b]) * x) + beta * x;
+    if (gamma != T(0)) y += gamma * Yold[idx];
+    Yold[idx] = y;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void fused_product(const FusedArgs& p, int nvl, const T* Ysrc, T* Ts, const T* Aop,
+                                              const T* Bop, int bsk, int bsn, const FusedEpi2<T>& e2) {
+  const int kA = p.kA, kB = p.kB, no = p.n_ops;
+  if (no > 0) {
+    cta_gemm<T>(nvl * kA, no * kB, kB, Ysrc, kB, 1, Bop, bsk, bsn, FusedEpi1<T>{Ts, kA, kB, nvl});
+    __syncthreads();
+  }
+  cta_gemm<T>(kA, nvl * kB, no * kA, Aop, no * kA, 1, Ts, nvl * kB, 1, e2);
+  __syncthreads();
+}
+
+// One launch: Out = normalised p(H) X (deg >= 1) or Out = H X (deg == 0).
+// X and Out may be the same array (each CTA reads its vectors before it
+// writes them).  HX is read only when compute_hx == 0 and deg >= 1.
+template <typename T>
+__global__ void __launch_bounds__(kFusedThreads)
+    cheb_fused_kernel(const T* X, const T* __restrict__ HX, const T* __restrict__ EA, const T* __restrict__ EB,
+                      const T* __restrict__ Acat, const T* __restrict__ Bcat, T* Out, FusedArgs p) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  T* sm = reinterpret_cast<T*>(fused_smem);
+  const int kA = p.kA, kB = p.kB, no = p.n_ops;
+  const int n = kA * kB;
+  const int v0 = blockIdx.x * p.vpc;
+  const int nvl = min(p.vpc, p.nv - v0);
+  if (nvl <= 0) return;
+  T* Yp = sm;                      // term k-1 (starts as X)
+  T* Yc = Yp + (size_t)p.vpc * n;  // term k
+  T* Ts = Yc + (size_t)p.vpc * n;  // stage-1 intermediate, n_ops * vpc * n
+  T* As = Ts + (size_t)no * p.vpc * n;
+  T* Bt = As + (size_t)kA * no * kA;
+  T* red = p.ops_in_smem ? Bt + (size_t)kB * no * kB : As;
+  const long base = (long)v0 * n;
+  const int cnt = nvl * n;
+  const T s1e = T(p.sigma1 / p.e);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const T x = X[base + i];
+    Yp[i] = x;
+    if (!p.compute_hx && p.deg >= 1) Yc[i] = s1e * (HX[base + i] - T(p.c) * x);
+  }
+  const T* Aop = Acat;
+  const T* Bop = Bcat;
+  int bsk = 1, bsn = kB;  // B(k, n') = Bcat[n' * kB + k]
+  if (p.ops_in_smem && no > 0) {
+    for (int i = threadIdx.x; i < kA * no * kA; i += blockDim.x) As[i] = Acat[i];
+    for (int i = threadIdx.x; i < no * kB * kB; i += blockDim.x) {
+      const int r = i / kB, k = i - r * kB;  // Bcat[r][k] -> Bt[k][r]
+      Bt[k * (no * kB) + r] = Bcat[i];
+    }
+    Aop = As;
+    Bop = Bt;
+    bsk = no * kB;
+    bsn = 1;
+  }
+  __syncthreads();
+  if (p.compute_hx || p.deg == 0) {
+    // Yc = a1 * (H Yp) + b1 * Yp: the first filter term, or the plain product
+    const T a1 = p.deg == 0 ? T(1) : s1e;
+    const T b1 = p.deg == 0 ? T(0) : T(-p.c) * s1e;
+    fused_product<T>(p, nvl, Yp, Ts, Aop, Bop, bsk, bsn, FusedEpi2<T>{Yp, Yc, EA, EB, kA, kB, a1, b1, T(0)});
+  }
+  double sigma = p.sigma1;
+  const double tau = 2.0 / p.sigma1;
+  for (int d = 2; d <= p.deg; ++d) {
+    const double s1 = 1.0 / (tau - sigma);
+    fused_product<T>(p, nvl, Yc, Ts, Aop, Bop, bsk, bsn,
+                     FusedEpi2<T>{Yc, Yp, EA, EB, kA, kB, T(2 * s1 / p.e), T(-2 * s1 * p.c / p.e), T(-sigma * s1)});
+    T* t = Yp;  // the new term was written over the old one
+    Yp = Yc;
+    Yc = t;
+    sigma = s1;
+  }
+  if (p.deg == 0) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) Out[base + i] = Yc[i];
+    return;
+  }
+  for (int v = 0; v < nvl; ++v) {
+    const T* y = Yc + (size_t)v * n;
+    T s = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += y[i] * y[i];
+    s = block_sum(s, red);
+    const T inv = s > T(0) ? T(1) / sqrt(s) : T(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Out[base + (long)v * n + i] = y[i] * inv;
+  }
+}
+
+}  // namespace rmc

@@ -30,6 +30,7 @@
 #include "../../include/rmc.h"
 #include "common.cuh"
 #include "gemm.cuh"
+#include "cheb_fused.cuh"
 #include "kernels.cuh"
 #include "umma.cuh"
 
@@ -345,6 +346,78 @@ rmc_status kron_work(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y,
       return kron_apply_tc(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
   }
   return kron_apply<T>(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
+}
+
+// Fused forms (one launch, vectors held in shared memory; see cheb_fused.cuh).
+// Plan: vectors per CTA (enough that a CTA has >= 2048 outputs per product,
+// within the shared-memory limit) and whether the operators are staged in
+// shared memory (FP32 only).  False when one vector does not fit.
+template <typename T>
+bool fused_plan(const KronOp<T>& H, int nv, FusedArgs* p, size_t* smem) {
+  const long n = H.n();
+  const int no = H.n_ops;
+  if (nv <= 0 || n <= 0) return false;
+  const size_t per_vec = (size_t)(2 + no) * n * sizeof(T);
+  const size_t red = 32 * sizeof(T);
+  size_t ops = (size_t)no * ((size_t)H.kA * H.kA + (size_t)H.kB * H.kB) * sizeof(T);
+  const bool ops_sm = sizeof(T) == 4 && no > 0 && ops + per_vec + red <= kFusedSmemLimit;
+  if (!ops_sm) ops = 0;
+  if (per_vec + ops + red > kFusedSmemLimit) return false;
+  const int fit = (int)((kFusedSmemLimit - ops - red) / per_vec);
+  const int vpc = (int)std::min<long>({(2048 + n - 1) / n, (long)fit, (long)nv});
+  *p = FusedArgs{H.kA, H.kB, no, nv, std::max(1, vpc), 0, 0, ops_sm ? 1 : 0, 0.0, 0.0, 0.0};
+  *smem = (size_t)p->vpc * per_vec + ops + red;
+  return true;
+}
+
+template <typename T>
+rmc_status launch_fused(rmc_ctx* ctx, const KronOp<T>& H, const T* X, const T* HX, T* Out, const FusedArgs& p,
+                        size_t smem, double flops) {
+  ProfScope ps(ctx, sizeof(T) == 8 ? 1 : 0, flops);
+  // process-wide attribute: raise to the limit once, never lower it
+  CK(cudaFuncSetAttribute(cheb_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit));
+  cheb_fused_kernel<T><<<ceil_div(p.nv, p.vpc), kFusedThreads, smem, ctx->stream>>>(X, HX, H.EA, H.EB, H.Acat,
+                                                                                       H.Bcat, Out, p);
+  CKL();
+  return RMC_OK;
+}
+
+inline double kron_flops_per_vector(int kA, int kB, int no) {
+  return (double)2 * no * kA * kB * (kA + kB) + 3.0 * kA * kB;
+}
+
+// Out = normalised p(H) X, p the degree-deg filter damping [a, ub] scaled at
+// theta0 (as cheb_filter, followed by column normalisation).  With hx_given
+// the product H X is read from HX, else formed in the kernel.  *done = false
+// when the block does not fit (nothing launched).
+template <typename T>
+rmc_status cheb_fused(rmc_ctx* ctx, const KronOp<T>& H, const T* X, const T* HX, int nv, int deg, double theta0,
+                      double a, double ub, T* Out, bool* done) {
+  *done = false;
+  FusedArgs p;
+  size_t smem;
+  if (sizeof(T) == 4 && ctx->cfg.precision == RMC_PREC_MIXED_TF32) return RMC_OK;  // tensor-core product
+  if (!fused_plan<T>(H, nv, &p, &smem)) return RMC_OK;
+  p.deg = std::max(1, deg);
+  p.compute_hx = HX ? 0 : 1;
+  p.e = (ub - a) / 2;
+  p.c = (ub + a) / 2;
+  p.sigma1 = p.e / (theta0 - p.c);
+  const double products = (double)(p.deg - 1 + p.compute_hx);
+  TRY(launch_fused<T>(ctx, H, X, HX, Out, p, smem, nv * products * kron_flops_per_vector(H.kA, H.kB, H.n_ops)));
+  *done = true;
+  return RMC_OK;
+}
+
+// Y = H X: the fused single-launch product when the block fits, else the
+// two-stage product (tensor cores for the TF32 working precision).
+template <typename T>
+rmc_status kron_product(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y, T* Tbuf) {
+  FusedArgs p;
+  size_t smem;
+  if (!(sizeof(T) == 4 && ctx->cfg.precision == RMC_PREC_MIXED_TF32) && fused_plan<T>(H, nv, &p, &smem))
+    return launch_fused<T>(ctx, H, X, nullptr, Y, p, smem, nv * kron_flops_per_vector(H.kA, H.kB, H.n_ops));
+  return kron_work<T>(ctx, H, X, nv, Y, T(1), T(0), T(0), nullptr, Tbuf);
 }
 
 // ---------------------------------------------------------------------------
@@ -739,7 +812,7 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
   CKL();
   auto rayleigh_ritz = [&]() -> rmc_status {
     Workspace wl(ctx);
-    TRY(kron_work<W>(ctx, H, X, b, HX, W(1), W(0), W(0), nullptr, Tbuf));
+    TRY(kron_product<W>(ctx, H, X, b, HX, Tbuf));
     TRY(gram<W>(ctx, wl, X, b, HX, b, n, G, true));
     if (fp64) {
       double* w64 = (double*)(void*)theta;
@@ -786,13 +859,17 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
     const double x0 = std::fabs((th[0] - c) / e);
     int deg = (int)std::floor(std::acosh(rho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
     deg = std::max(2, std::min(dmax, deg));
-    W* Yout = nullptr;
-    TRY((cheb_filter<W>(ctx, H, X, HX, b, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout)));
-    W* Ycur = Yout;
-    // X <- normalised, orthonormalised filter output
-    CK(cudaMemcpyAsync(X, Ycur, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    normalize_kernel<W><<<b, 256, 0, ctx->stream>>>(X, n, nullptr);
-    CKL();
+    // X <- normalised filter output (one fused launch when the block fits),
+    // then orthonormalised
+    bool fused = false;
+    TRY(cheb_fused<W>(ctx, H, X, HX, b, deg, th[0], a, ub, X, &fused));
+    if (!fused) {
+      W* Yout = nullptr;
+      TRY((cheb_filter<W>(ctx, H, X, HX, b, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout)));
+      CK(cudaMemcpyAsync(X, Yout, sizeof(W) * b * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      normalize_kernel<W><<<b, 256, 0, ctx->stream>>>(X, n, nullptr);
+      CKL();
+    }
     {
       Workspace wl(ctx);
       TRY(cholqr<W>(ctx, wl, X, b, n, tmp, fp64 ? 1e-14 : 1e-6));
@@ -1129,7 +1206,7 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
           normalize_kernel<double><<<nc, 256, 0, ctx->stream>>>(Xc, n, nullptr);
           CKL();
           TRY(cholqr<double>(ctx, wc, Xc, nc, n, tmp64, 1e-14));
-          TRY(kron_apply<double>(ctx, H64, Xc, nc, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+          TRY(kron_product<double>(ctx, H64, Xc, nc, HX64, Tb64));
           TRY(gram<double>(ctx, wc, Xc, nc, HX64, nc, n, Gc, true));
           TRY(syev64(ctx, wc, Gc, nc, wcv, Zc));
           TRY(combine<double>(ctx, Zc, true, nc, nc, Xc, n, tmp64, 1.0, 0.0, nullptr));
@@ -1139,23 +1216,27 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
     } else if (refine) {
       const double a = th_cur[bf - 1], e = (ub - a) / 2, cc = (ub + a) / 2;
       if (e > 0) {
-        Workspace wp(ctx);
-        double *Y0, *Y1, *Y2, *Yout = nullptr;
-        TRY(wp.get(&Y0, (size_t)bf * n));
-        TRY(wp.get(&Y1, (size_t)bf * n));
-        TRY(wp.get(&Y2, (size_t)bf * n));
         const double x0 = std::fabs((th_cur[0] - cc) / e);
         int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
         deg = std::max(2, std::min(16, deg));
-        TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
-        TRY((cheb_filter<double>(ctx, H64, X64, HX64, bf, th_cur[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
-        CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        normalize_kernel<double><<<bf, 256, 0, ctx->stream>>>(X64, n, nullptr);
-        CKL();
+        bool fused = false;
+        TRY(cheb_fused<double>(ctx, H64, X64, nullptr, bf, deg, th_cur[0], a, ub, X64, &fused));
+        if (!fused) {
+          Workspace wp(ctx);
+          double *Y0, *Y1, *Y2, *Yout = nullptr;
+          TRY(wp.get(&Y0, (size_t)bf * n));
+          TRY(wp.get(&Y1, (size_t)bf * n));
+          TRY(wp.get(&Y2, (size_t)bf * n));
+          TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+          TRY((cheb_filter<double>(ctx, H64, X64, HX64, bf, th_cur[0], a, ub, deg, Y0, Y1, Y2, Tb64, &Yout)));
+          CK(cudaMemcpyAsync(X64, Yout, sizeof(double) * bf * n, cudaMemcpyDeviceToDevice, ctx->stream));
+          normalize_kernel<double><<<bf, 256, 0, ctx->stream>>>(X64, n, nullptr);
+          CKL();
+        }
       }
     }
     TRY(cholqr64_refine(ctx, ws, X64, bf, n, tmp64));
-    TRY(kron_apply<double>(ctx, H64, X64, bf, HX64, 1.0, 0.0, 0.0, nullptr, Tb64));
+    TRY(kron_product<double>(ctx, H64, X64, bf, HX64, Tb64));
     TRY(gram<double>(ctx, ws, X64, bf, HX64, bf, n, Gs, true));
     TRY(syev64(ctx, ws, Gs, bf, w, Zs, chunked));
     TRY(combine<double>(ctx, Zs, true, bf, bf, X64, n, C, 1.0, 0.0, nullptr));
@@ -1567,6 +1648,73 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
                              (const float*)Z, Tbuf);
     }
     return kron_apply<T>(ctx, H, (const T*)X, nv, (T*)Y, (T)alpha, (T)beta, (T)gamma, (const T*)Z, Tbuf);
+  };
+  return dtype == 0 ? run(double{}) : run(float{});
+}
+
+rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv, const void* EA,
+                           const void* EB, const void* A, const void* B, const double* coef, const void* X, int deg,
+                           double theta0, double a, double ub, int fused, void* Y) {
+  TRY(check_ctx(ctx));
+  if (kA < 1 || kB < 1 || n_ops < 0 || n_ops > kMaxOps || nv < 1 || !EA || !EB || !X || !Y ||
+      (n_ops && (!A || !B || !coef)) || dtype < 0 || dtype > 1 || deg < 0 || deg > 64 || (fused != 0 && fused != 1))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: bad arguments");
+  if (deg > 0 && !(theta0 < a && a < ub)) return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: need theta0 < a < ub");
+  Workspace ws(ctx);
+  Coefs cf{};
+  for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
+  auto run = [&](auto tag) -> rmc_status {
+    using T = decltype(tag);
+    const long n = (long)kA * kB;
+    KronOp<T> H;
+    H.kA = kA;
+    H.kB = kB;
+    H.n_ops = n_ops;
+    H.EA = (const T*)EA;
+    H.EB = (const T*)EB;
+    H.Bcat = (const T*)B;
+    T* Acat;
+    TRY(ws.get(&Acat, (size_t)std::max(1, n_ops) * kA * kA));
+    if (n_ops) {
+      build_acat_kernel<T><<<grid1d((long)kA * kA * n_ops), 256, 0, ctx->stream>>>((const T*)A, cf, kA, n_ops, Acat);
+      CKL();
+    }
+    H.Acat = Acat;
+    if (fused) {
+      FusedArgs p;
+      size_t smem;
+      if (!fused_plan<T>(H, nv, &p, &smem))
+        return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: a %d x %d vector does not fit the fused kernel", kA, kB);
+      if (deg == 0) return launch_fused<T>(ctx, H, (const T*)X, nullptr, (T*)Y, p, smem, 0.0);
+      p.deg = deg;
+      p.compute_hx = 1;
+      p.e = (ub - a) / 2;
+      p.c = (ub + a) / 2;
+      p.sigma1 = p.e / (theta0 - p.c);
+      return launch_fused<T>(ctx, H, (const T*)X, nullptr, (T*)Y, p, smem, 0.0);
+    }
+    T *Tbuf, *HX, *Y0, *Y1, *Y2;
+    TRY(ws.get(&Tbuf, (size_t)std::max(1, n_ops) * n * nv));
+    if (deg == 0) return kron_apply<T>(ctx, H, (const T*)X, nv, (T*)Y, T(1), T(0), T(0), nullptr, Tbuf);
+    TRY(ws.get(&HX, (size_t)n * nv));
+    TRY(ws.get(&Y0, (size_t)n * nv));
+    TRY(ws.get(&Y1, (size_t)n * nv));
+    TRY(ws.get(&Y2, (size_t)n * nv));
+    TRY(kron_apply<T>(ctx, H, (const T*)X, nv, HX, T(1), T(0), T(0), nullptr, Tbuf));
+    T* Yout = nullptr;
+    if (deg == 1) {
+      const double e = (ub - a) / 2, c = (ub + a) / 2, s1 = e / (theta0 - c);
+      axpby_kernel<T><<<grid1d((long)nv * n), 256, 0, ctx->stream>>>(HX, (const T*)X, (long)nv * n, T(s1 / e),
+                                                                      T(-c * s1 / e), Y1);
+      CKL();
+      Yout = Y1;
+    } else {
+      TRY((cheb_filter<T>(ctx, H, (const T*)X, HX, nv, theta0, a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout)));
+    }
+    CK(cudaMemcpyAsync(Y, Yout, sizeof(T) * n * nv, cudaMemcpyDeviceToDevice, ctx->stream));
+    normalize_kernel<T><<<nv, 256, 0, ctx->stream>>>((T*)Y, n, nullptr);
+    CKL();
+    return RMC_OK;
   };
   return dtype == 0 ? run(double{}) : run(float{});
 }

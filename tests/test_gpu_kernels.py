@@ -2,6 +2,8 @@
 
 * Kronecker-form product (Eq. (7)) against the oracle's dense H_eff times X,
   including the Chebyshev three-term form alpha H X + beta X + gamma Z.
+* Chebyshev filter (single-launch shared-memory form and multi-launch form)
+  against the scaled three-term recurrence on the oracle's dense H_eff.
 * Small symmetric eigensolver (FP32 Jacobi + FP64 refinement) against LAPACK.
 * Operator rotation against C^T kron(o, I) C / C^T kron(I, o) C.
 """
@@ -61,6 +63,85 @@ def test_kron_matvec_matches_dense_heff(ctx, kA, kB, n_ops, nv, dtype):
         scale = max(1.0, np.abs(ref).max())
         tol = 1e-12 if dtype == 0 else 3e-5
         assert np.abs(got - ref).max() <= tol * scale, (alpha, beta, gamma, np.abs(got - ref).max() / scale)
+
+
+def _dense_filter(H, X, deg, theta0, a, ub):
+    """Scaled Chebyshev filter (Zhou and Saad) written out on the dense H,
+    then column normalisation; deg = 0 is the plain product."""
+    nv = X.shape[0]
+    Xf = X.reshape(nv, -1)
+    if deg == 0:
+        return (Xf @ H.T).reshape(X.shape)
+    e, c = (ub - a) / 2, (ub + a) / 2
+    sigma1 = e / (theta0 - c)
+    Y0, Y1 = Xf, (sigma1 / e) * (Xf @ H.T - c * Xf)
+    sigma, tau = sigma1, 2.0 / sigma1
+    for _ in range(2, deg + 1):
+        s1 = 1.0 / (tau - sigma)
+        Y0, Y1 = Y1, (2 * s1 / e) * (Y1 @ H.T - c * Y1) - sigma * s1 * Y0
+        sigma = s1
+    Y1 = Y1 / np.linalg.norm(Y1, axis=1, keepdims=True)
+    return Y1.reshape(X.shape)
+
+
+FILTER_CASES = [(16, 16, 3, 40, 8), (64, 64, 3, 9, 6), (24, 40, 1, 7, 5), (7, 13, 2, 3, 1), (64, 64, 0, 5, 4),
+                (20, 30, 3, 6, 0), (62, 60, 3, 11, 12), (1, 1, 1, 2, 3)]
+
+
+@pytest.mark.parametrize("kA,kB,n_ops,nv,deg", FILTER_CASES)
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("fused", [True, False])
+def test_chebyshev_filter_matches_dense_recurrence(ctx, kA, kB, n_ops, nv, deg, dtype, fused):
+    """Both forms of the filter against the recurrence on the dense H_eff:
+    damped interval [theta_m, ub] from the exact spectrum, scaled at its lowest
+    eigenvalue; ragged shapes, several vectors per CTA, no coupling, degrees
+    0 (plain product), 1 and up to 12."""
+    rng = np.random.default_rng(kA * 7919 + kB * 31 + n_ops * 7 + nv + deg)
+    EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
+    H = O.effective_hamiltonian(EA, EB, [(coef[j], oA[j], oB[j]) for j in range(n_ops)])
+    lam = np.linalg.eigvalsh(H)
+    m = min(len(lam) - 1, max(1, len(lam) // 4))
+    theta0, a, ub = lam[0] - 1e-3, lam[m] + 1e-3, lam[-1] + 0.1
+    X = rng.standard_normal((nv, kA, kB))
+    ref = _dense_filter(H, X, deg, theta0, a, ub)
+    npdt = np.float64 if dtype == 0 else np.float32
+    d = [dev(v, npdt) for v in (EA, EB, oA, oB, X)]
+    Y = dev(np.zeros_like(X), npdt)
+    torch_cuda().cuda.synchronize()
+    ctx.cheb_filter(dtype, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(),
+                    coef, d[4].data_ptr(), deg, theta0, a, ub, fused, Y.data_ptr())
+    got = host(Y)
+    scale = max(1.0, np.abs(ref).max())
+    tol = 1e-11 if dtype == 0 else 2e-4
+    assert np.abs(got - ref).max() <= tol * scale, np.abs(got - ref).max() / scale
+
+
+def test_chebyshev_filter_in_place_and_limits(ctx):
+    """Y may alias X; the single-launch form rejects vectors it cannot hold
+    (128 x 128 with three operators); theta0 < a < ub is required."""
+    rng = np.random.default_rng(5)
+    kA, kB, n_ops, nv = 16, 12, 2, 5
+    EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
+    H = O.effective_hamiltonian(EA, EB, [(coef[j], oA[j], oB[j]) for j in range(n_ops)])
+    lam = np.linalg.eigvalsh(H)
+    X = rng.standard_normal((nv, kA, kB))
+    ref = _dense_filter(H, X, 5, lam[0], lam[20], lam[-1] + 0.1)
+    d = [dev(v, np.float64) for v in (EA, EB, oA, oB, X)]
+    torch_cuda().cuda.synchronize()
+    ctx.cheb_filter(0, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(), coef,
+                    d[4].data_ptr(), 5, lam[0], lam[20], lam[-1] + 0.1, True, d[4].data_ptr())
+    assert np.abs(host(d[4]) - ref).max() <= 1e-11
+    big = [dev(np.zeros(s), np.float32) for s in (128, 128, (3, 128, 128), (3, 128, 128), (2, 128, 128))]
+    torch_cuda().cuda.synchronize()
+    with pytest.raises(P.RmcError) as e:
+        ctx.cheb_filter(1, 128, 128, 3, 2, big[0].data_ptr(), big[1].data_ptr(), big[2].data_ptr(),
+                        big[3].data_ptr(), [1.0, 1.0, 1.0], big[4].data_ptr(), 3, -2.0, -1.0, 1.0, True,
+                        big[4].data_ptr())
+    assert e.value.status == P.RMC_ERR_INVAL
+    with pytest.raises(P.RmcError) as e:
+        ctx.cheb_filter(0, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(),
+                        coef, d[4].data_ptr(), 3, 1.0, 0.5, 2.0, False, d[4].data_ptr())
+    assert e.value.status == P.RMC_ERR_INVAL
 
 
 def test_tensor_core_product_rejects_shapes_it_cannot_hold(ctx):
