@@ -101,6 +101,30 @@ def xxz(n: int, Js: Sequence[float], delta: float, leaf_sites: int, k: int, q: i
     return Chain(n, onsite, bonds, leaf_sites, k, q, name or f"xxz_N{n}_D{delta}")
 
 
+def two_module_tfim(geometry: str, Jp: float, k: int, q: int = 4, J: float = 1.0, h: float = 0.7,
+                    gamma: float = 0.2) -> Chain:
+    """Two five-site Ising modules (the block Hamiltonian of Appendix C) joined
+    by one inter-module ZZ coupling -Jp at the sites of geometry I (A5-B1),
+    II (A5-B2), III (A5-B3) or IV (A3-B3), 1-based within each module, or by
+    the next-nearest form 'NNN': -Jp (A5-B1 + gamma A4-B1 + gamma A5-B2)."""
+    onsite = [(i, "X", -float(h)) for i in range(10)]
+    bonds: List[Bond] = [(i, i + 1, "Z", "Z", -float(J)) for m in (0, 5) for i in range(m, m + 4)]
+    pairs = {"I": [(5, 1, 1.0)], "II": [(5, 2, 1.0)], "III": [(5, 3, 1.0)], "IV": [(3, 3, 1.0)],
+             "NNN": [(5, 1, 1.0), (4, 1, gamma), (5, 2, gamma)]}[geometry]
+    for a, b, w in pairs:
+        bonds.append((a - 1, 5 + b - 1, "Z", "Z", -float(Jp) * w))
+    return Chain(10, onsite, bonds, 5, k, q, f"tfim2x5_{geometry}_Jp{Jp:.3g}_k{k}")
+
+
+def tfim_nnn(n: int, J: float, h: float, gamma: float, leaf_sites: int, k: int, q: int) -> Chain:
+    """Ising chain with next-nearest ZZ couplings of relative strength gamma,
+    H = -J sum (Z_i Z_{i+1} + gamma Z_i Z_{i+2}) - h sum X_i."""
+    onsite = [(i, "X", -float(h)) for i in range(n)]
+    bonds: List[Bond] = [(i, i + 1, "Z", "Z", -float(J)) for i in range(n - 1)]
+    bonds += [(i, i + 2, "Z", "Z", -float(J) * float(gamma)) for i in range(n - 2)]
+    return Chain(n, onsite, bonds, leaf_sites, k, q, f"tfim_nnn_N{n}_g{gamma:.3g}_L{leaf_sites}_k{k}")
+
+
 def seed_for(config_index: int) -> int:
     """Seed of workload ``config_index`` (1-based): 2609*100 + index."""
     return 2609 * 100 + config_index

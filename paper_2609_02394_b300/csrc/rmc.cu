@@ -1768,9 +1768,17 @@ struct CTerm {  // on-site (j < 0) or two-site term with chain-global sites
 struct ChainNode {
   int lo, hi;
   int left = -1, right = -1;
+  bool sub = false;  // piece of a leaf wider than the dense leaf solver: keeps all its states
   std::string sig;
   std::vector<std::pair<int, char>> carry;  // relative (site, pauli), sorted
 };
+
+// Widest leaf the dense leaf solver takes (D = 2^7 = 128 <= the small
+// eigensolver's 160).  A wider leaf (up to twice this) is built exactly as
+// two dense sub-leaves that keep all their states and one merge that keeps
+// min(k, D): the merge's product space is the leaf's whole Hilbert space, so
+// its lowest states are the leaf's (Algorithm 1, first step, for L0 up to 14).
+constexpr int kDenseLeafSites = 7;
 
 int build_tree(std::vector<ChainNode>& nodes, int lo, int hi, int L0) {
   nodes.push_back(ChainNode{lo, hi});
@@ -1830,13 +1838,30 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
     terms.push_back(CTerm{bond_i[t], bond_j[t], (char)toupper(bond_pauli_i[t]), (char)toupper(bond_pauli_j[t]),
                           bond_coef[t]});
   }
+  if (L0 > 2 * kDenseLeafSites)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: leaves of more than %d sites are not supported",
+                2 * kDenseLeafSites);
   std::vector<ChainNode> nodes;
   build_tree(nodes, 0, n_sites, L0);
+  const size_t n_tree = nodes.size();
+  for (size_t id = 0; id < n_tree; ++id) {
+    if (nodes[id].left >= 0 || nodes[id].hi - nodes[id].lo <= kDenseLeafSites) continue;
+    const int lo = nodes[id].lo, hi = nodes[id].hi, mid = lo + (hi - lo) / 2;
+    if (id != 0 && k >= (1 << (hi - lo)))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: k = %d keeps a whole %d-site leaf; use k < %d", k, hi - lo,
+                  1 << (hi - lo));
+    ChainNode l{lo, mid}, r{mid, hi};
+    l.sub = r.sub = true;
+    nodes.push_back(l);
+    nodes.push_back(r);
+    nodes[id].left = (int)nodes.size() - 2;
+    nodes[id].right = (int)nodes.size() - 1;
+  }
   // carried operators per node: inside ends of terms crossing its boundary;
   // nodes with one signature carry the union so one block serves them all.
   std::map<std::string, std::set<std::pair<int, char>>> need;
   for (ChainNode& nd : nodes) {
-    nd.sig = signature(terms, nd.lo, nd.hi);
+    nd.sig = (nd.sub ? std::string("all|") : std::string()) + signature(terms, nd.lo, nd.hi);
     auto& st = need[nd.sig];
     for (const CTerm& t : terms) {
       if (t.j < 0) continue;
@@ -1873,7 +1898,7 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
       }
       std::vector<rmc_op_tag> cr;
       for (auto& c : nd.carry) cr.push_back(rmc_op_tag{c.first, c.second});
-      TRY(rmc_build_leaf_pauli(ctx, L, top ? (1 << L) : k, (int)os.size(), os.data(), op.data(), oc.data(),
+      TRY(rmc_build_leaf_pauli(ctx, L, (top || nd.sub) ? (1 << L) : k, (int)os.size(), os.data(), op.data(), oc.data(),
                                (int)bi.size(), bi.data(), bj.data(), pi.data(), pj.data(), bc.data(), (int)cr.size(),
                                cr.data(), &blk));
     } else {

@@ -92,3 +92,44 @@ def test_degenerate_k256_chain_mixed_agrees_with_fp64():
         ref = c64.solve_chain(c)
         got = cm.solve_chain(c)
     assert np.all(np.abs(got - ref) <= 1e-8 * np.maximum(1.0, np.abs(ref))), got - ref
+
+
+WIDE_LEAF_CHAINS = [
+    I.tfim(18, 1.0, 0.9, 9, 64, 4),                       # two 9-site leaves (D = 512): 4 + 5 sub-leaves each
+    I.xxz(16, list(np.random.default_rng(41).uniform(0.5, 1.5, 15)), 1.0, 8, 48, 4),  # 8-site leaves (D = 256)
+    I.tfim(9, 1.0, 0.8, 9, 64, 4),                        # the whole chain is one 9-site leaf
+]
+
+
+@pytest.mark.parametrize("chain", WIDE_LEAF_CHAINS, ids=lambda c: c.name)
+def test_wide_leaves_match_oracle(ctx, chain):
+    """Leaves wider than the dense leaf solver (L0 = 8, 9: D = 256, 512) are
+    built as two dense sub-leaves keeping every state plus one merge keeping
+    min(k, D); the oracle diagonalises the D x D leaf densely (Algorithm 1,
+    first step)."""
+    _close(ctx, ctx.solve_chain(chain), O.solve(chain).energies)
+
+
+GEOMETRY_CHAINS = [I.two_module_tfim(g, jp, k) for g, jp, k in
+                   [("I", 0.8, 8), ("II", 0.8, 8), ("III", 1.0, 10), ("IV", 0.6, 8), ("NNN", 0.8, 10)]] + [
+    I.tfim_nnn(20, 1.0, 0.7, 0.2, 5, 16, 4),   # next-nearest bonds across every boundary
+    I.tfim_nnn(24, 1.0, 1.0, 0.2, 3, 32, 4),   # leaves of 3: carried operators on interior sites
+]
+
+
+@pytest.mark.parametrize("chain", GEOMETRY_CHAINS, ids=lambda c: c.name)
+def test_coupling_geometries_match_oracle(ctx, chain):
+    """The inter-module coupling geometries of Appendix C (A5-B1, A5-B2,
+    A5-B3, A3-B3 and the next-nearest form with gamma = 0.2) and whole chains
+    with next-nearest couplings: every term crossing a boundary carries its
+    inside end, wherever that site is in the block."""
+    _close(ctx, ctx.solve_chain(chain), O.solve(chain).energies)
+
+
+def test_leaf_limits_are_rejected(ctx):
+    with pytest.raises(P.RmcError) as e:
+        ctx.solve_chain(I.tfim(16, 1.0, 0.9, 8, 256, 4))   # k keeps a whole 8-site leaf
+    assert e.value.status == P.RMC_ERR_INVAL
+    with pytest.raises(P.RmcError) as e:
+        ctx.solve_chain(I.tfim(30, 1.0, 0.9, 15, 16, 4))   # leaves of 15 sites
+    assert e.value.status == P.RMC_ERR_INVAL
