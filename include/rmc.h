@@ -219,6 +219,26 @@ typedef struct rmc_chain {
   const double* bond_coef;
 } rmc_chain;
 
+/* The chain solve of rmc_solve_chain (for `chain`, described as for the
+ * server below) with two optional products for its q lowest states |psi_mu>:
+ *   obs_out[o][mu][nu] = <psi_mu| O_o |psi_nu>   (n_obs x q x q, host)
+ * for the single-site Pauli observables obs[o] ('X', 'Z', or 'Y' given as the
+ * real antisymmetric iY, so the result is -i<psi_mu|Y|psi_nu>): each is
+ * carried through every basis rotation on its way to the top block (Sec. II,
+ * the projected operators of Algorithm 1), so it costs one k x k operator per
+ * block and works at any chain length; and
+ *   psi_out[mu][x] = the state lifted to the 2^n_sites computational basis
+ * (x = sum_s bit_s 2^(n_sites-1-s), site 0 most significant; the recursive
+ * product of Eq. (11) psi = (U_A (x) U_B) C), for n_sites <= 24 (else
+ * RMC_ERR_INVAL), q x 2^n_sites host doubles.  Either may be NULL (obs_out
+ * only when n_obs = 0).  States beyond the top block's kept count are NaN.
+ * Observed sites make their blocks distinct from unobserved twins, so
+ * homogeneous reuse covers fewer blocks.  The paper has these as the
+ * fidelities of Sec. III A and the state-lifting of Eq. (11).  Synchronises. */
+rmc_status rmc_solve_chain_states(rmc_ctx* ctx, const struct rmc_chain* chain, int n_obs,
+                                  const rmc_op_tag* obs, double* E_out, double* obs_out,
+                                  double* psi_out);
+
 typedef struct rmc_server rmc_server;
 
 /* A solve server: `slots` solves run at once, each on its own host worker

@@ -29,7 +29,7 @@ EXPORTED = [
     "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
     "rmc_kron_matvec_noalloc", "rmc_server_create", "rmc_server_destroy", "rmc_submit", "rmc_poll",
     "rmc_server_stats", "rmc_estimate_bytes", "rmc_solve_chains", "rmc_server_profile",
-    "rmc_server_profile_read", "rmc_server_last_error", "rmc_cheb_filter",
+    "rmc_server_profile_read", "rmc_server_last_error", "rmc_cheb_filter", "rmc_solve_chain_states",
 ]
 PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
@@ -131,6 +131,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_kron_matvec_noalloc": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
         "rmc_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
         "rmc_cheb_filter": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, ip, dp, dp, dp, ip, vp], ip),
+        "rmc_solve_chain_states": ([vp, P(rmc_chain), ip, P(rmc_op_tag), P(dp), P(dp), P(dp)], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -334,6 +335,25 @@ class Context:
             "".join(t[3] for t in bnd).encode(), _dptr(_f64([t[4] for t in bnd])), _dptr(E))
         self._check(st)
         return E
+
+    def solve_chain_states(self, chain, observables=(), states: bool = False):
+        """The chain solve plus <psi_mu|O|psi_nu> for single-site Pauli
+        observables [(site, 'X'|'Y'|'Z'), ...] (Y as iY) and, with
+        ``states``, the lowest q states lifted to the 2^N basis (N <= 24).
+        Returns (E[q], O[n_obs, q, q], psi[q, 2^N] or None)."""
+        c, keep = make_chain(chain)
+        q = chain.q
+        E = np.full(q, np.nan)
+        n_obs = len(observables)
+        tags = (rmc_op_tag * max(1, n_obs))(*[rmc_op_tag(int(s_), p.encode()) for s_, p in observables])
+        O = np.full((max(1, n_obs), q, q), np.nan)
+        # (more than 24 sites: the library rejects the request before writing)
+        psi = np.full((q, 1 << min(chain.n_sites, 24)), np.nan) if states else None
+        st = self.lib.rmc_solve_chain_states(self.h, ctypes.byref(c), n_obs, tags, _dptr(E),
+                                             _dptr(O) if n_obs else None, _dptr(psi) if states else None)
+        del keep
+        self._check(st)
+        return E, O[:n_obs], psi
 
     # ---- kernel-level entry points (device pointers) -------------------------
     def kron_matvec(self, dtype: int, kA: int, kB: int, n_ops: int, nv: int, EA: int, EB: int, A: int, B: int,

@@ -1780,6 +1780,10 @@ struct ChainNode {
 // its lowest states are the leaf's (Algorithm 1, first step, for L0 up to 14).
 constexpr int kDenseLeafSites = 7;
 
+// Largest chain whose lowest states rmc_solve_chain_states lifts to the full
+// 2^N computational basis (2^24 doubles = 128 MiB per state).
+constexpr int kMaxLiftSites = 24;
+
 int build_tree(std::vector<ChainNode>& nodes, int lo, int hi, int L0) {
   nodes.push_back(ChainNode{lo, hi});
   const int id = (int)nodes.size() - 1;
@@ -1819,13 +1823,56 @@ int find_tag(const rmc_block* b, int site, char p) {
 
 }  // namespace
 
-extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int n_onsite,
-                                      const int* onsite_site, const char* onsite_pauli, const double* onsite_coef,
-                                      int n_bonds, const int* bond_i, const int* bond_j, const char* bond_pauli_i,
-                                      const char* bond_pauli_j, const double* bond_coef, double* E_out) {
+namespace {
+
+// Lifted states of a block (Eq. (11) applied recursively, psi = (U_A (x) U_B) C):
+// out (k x 2^L, vector-major) for a block of L sites.  Leaf: its basis.
+// Merge: for each kept vector c_j (a k_A x k_B matrix), psi_j = U_A^T c_j U_B
+// with U_A, U_B the children's lifted states, in two batched GEMMs.
+rmc_status lift_block(rmc_ctx* ctx, Workspace& ws, const std::vector<ChainNode>& nodes,
+                      const std::vector<rmc_block*>& blk_of, int id, int kuse, double** out) {
+  const ChainNode& nd = nodes[id];
+  const rmc_block* b = blk_of[id];
+  const long len = 1L << (nd.hi - nd.lo);
+  if (nd.left < 0) {
+    *out = b->basis;
+    return RMC_OK;
+  }
+  double *UA, *UB;
+  TRY(lift_block(ctx, ws, nodes, blk_of, nd.left, blk_of[nd.left]->k, &UA));
+  TRY(lift_block(ctx, ws, nodes, blk_of, nd.right, blk_of[nd.right]->k, &UB));
+  const int kA = blk_of[nd.left]->k, kB = blk_of[nd.right]->k;
+  const long LA = 1L << (nodes[nd.left].hi - nodes[nd.left].lo), LB = len / LA;
+  double *T, *Psi;
+  TRY(ws.get(&T, (size_t)kuse * kA * LB));
+  TRY(ws.get(&Psi, (size_t)kuse * len));
+  // T[(j, a)][y] = sum_b C[j][a][b] U_B[b][y]
+  GemmShape s1{kuse * kA, (int)LB, kB, kB, LB, 0, 0, 1};
+  gemm_big<double, false, false>(b->basis, UB, s1, 1, EpiAxpby<double>{T, nullptr, LB, 0, 0, 0, 1.0, 0.0},
+                                 ctx->stream);
+  CKL();
+  // Psi_j[x][y] = sum_a U_A[a][x] T_j[a][y]
+  GemmShape s2{(int)LA, (int)LB, kA, LA, LB, 0, (long)kA * LB, 1};
+  gemm_big<double, true, false>(UA, T, s2, kuse, EpiAxpby<double>{Psi, nullptr, LB, 0, len, 0, 1.0, 0.0},
+                                ctx->stream);
+  CKL();
+  *out = Psi;
+  return RMC_OK;
+}
+
+// The recursion loop of Algorithm 1 over a chain, optionally carrying extra
+// single-site operators (observables) to the top and lifting the top states.
+rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int n_onsite, const int* onsite_site,
+                            const char* onsite_pauli, const double* onsite_coef, int n_bonds, const int* bond_i,
+                            const int* bond_j, const char* bond_pauli_i, const char* bond_pauli_j,
+                            const double* bond_coef, int n_obs, const rmc_op_tag* obs, double* E_out,
+                            double* obs_out, double* psi_out) {
   TRY(check_ctx(ctx));
-  if (n_sites < 1 || L0 < 1 || k < 1 || q < 1 || n_onsite < 0 || n_bonds < 0 || !E_out)
+  if (n_sites < 1 || L0 < 1 || k < 1 || q < 1 || n_onsite < 0 || n_bonds < 0 || !E_out || n_obs < 0 ||
+      (n_obs > 0 && (!obs || !obs_out)))
     return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: bad arguments");
+  if (psi_out && n_sites > kMaxLiftSites)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_states: lifting needs n_sites <= %d", kMaxLiftSites);
   std::vector<CTerm> terms;
   for (int t = 0; t < n_onsite; ++t) {
     if (onsite_site[t] < 0 || onsite_site[t] >= n_sites)
@@ -1837,6 +1884,13 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
       return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: bond %d out of range", t);
     terms.push_back(CTerm{bond_i[t], bond_j[t], (char)toupper(bond_pauli_i[t]), (char)toupper(bond_pauli_j[t]),
                           bond_coef[t]});
+  }
+  std::vector<std::pair<int, char>> observables;
+  for (int o = 0; o < n_obs; ++o) {
+    const char p = (char)toupper(obs[o].pauli);
+    if (obs[o].site < 0 || obs[o].site >= n_sites || (p != 'X' && p != 'Y' && p != 'Z'))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_states: observable %d is not a site Pauli", o);
+    observables.push_back({obs[o].site, p});
   }
   if (L0 > 2 * kDenseLeafSites)
     return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: leaves of more than %d sites are not supported",
@@ -1857,8 +1911,9 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
     nodes[id].left = (int)nodes.size() - 2;
     nodes[id].right = (int)nodes.size() - 1;
   }
-  // carried operators per node: inside ends of terms crossing its boundary;
-  // nodes with one signature carry the union so one block serves them all.
+  // carried operators per node: inside ends of terms crossing its boundary,
+  // plus every observable on its sites (rotated up to the top); nodes with
+  // one signature carry the union so one block serves them all.
   std::map<std::string, std::set<std::pair<int, char>>> need;
   for (ChainNode& nd : nodes) {
     nd.sig = (nd.sub ? std::string("all|") : std::string()) + signature(terms, nd.lo, nd.hi);
@@ -1870,10 +1925,28 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
       if (jin && !iin) st.insert({t.j - nd.lo, t.pj});
     }
   }
+  // observables: a site's operator rides on every block containing it; the
+  // signature gains the observed sites so that such blocks are not shared
+  // with unobserved twins elsewhere in the chain
+  if (!observables.empty()) {
+    for (ChainNode& nd : nodes) {
+      std::string extra;
+      for (auto& o : observables)
+        if (o.first >= nd.lo && o.first < nd.hi) extra += std::to_string(o.first - nd.lo) + o.second + ",";
+      if (extra.empty()) continue;
+      auto base = need[nd.sig];
+      nd.sig = "obs:" + extra + "|" + nd.sig;
+      auto& st = need[nd.sig];
+      st.insert(base.begin(), base.end());
+      for (auto& o : observables)
+        if (o.first >= nd.lo && o.first < nd.hi) st.insert({o.first - nd.lo, o.second});
+    }
+  }
   for (ChainNode& nd : nodes) nd.carry.assign(need[nd.sig].begin(), need[nd.sig].end());
 
   std::map<std::string, rmc_block*> cache;
   std::vector<rmc_block*> owned;
+  std::vector<rmc_block*> blk_of(nodes.size(), nullptr);
   rmc_status soft = RMC_OK;
   auto cleanup = [&]() {
     for (rmc_block* b : owned) free_block(ctx, b);
@@ -1882,7 +1955,28 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
     const ChainNode& nd = nodes[id];
     if (!top) {
       auto it = cache.find(nd.sig);
-      if (it != cache.end()) { *out = it->second; return RMC_OK; }
+      if (it != cache.end()) {
+        *out = blk_of[id] = it->second;
+        // the shared block's children serve this node's lifting too
+        if (nd.left >= 0) {
+          for (size_t o = 0; o < nodes.size(); ++o)
+            if (blk_of[o] == it->second && nodes[o].left >= 0 && (int)o != id) {
+              blk_of[nd.left] = blk_of[nodes[o].left];
+              blk_of[nd.right] = blk_of[nodes[o].right];
+              std::function<void(int, int)> copy_sub = [&](int dst, int src) {
+                blk_of[dst] = blk_of[src];
+                if (nodes[dst].left >= 0 && nodes[src].left >= 0) {
+                  copy_sub(nodes[dst].left, nodes[src].left);
+                  copy_sub(nodes[dst].right, nodes[src].right);
+                }
+              };
+              copy_sub(nd.left, nodes[o].left);
+              copy_sub(nd.right, nodes[o].right);
+              break;
+            }
+        }
+        return RMC_OK;
+      }
     }
     rmc_block* blk = nullptr;
     if (nd.left < 0) {
@@ -1915,13 +2009,11 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
         mt.push_back(rmc_term{(t.pi == 'Y' && t.pj == 'Y') ? -t.coef : t.coef, oa, ob});
       }
       std::vector<rmc_carry> cy;
-      if (!top) {
-        for (auto& c : nd.carry) {
-          const int gsite = nd.lo + c.first;
-          if (gsite < Blo) cy.push_back(rmc_carry{0, find_tag(A, gsite - Alo, c.second)});
-          else cy.push_back(rmc_carry{1, find_tag(B, gsite - Blo, c.second)});
-          if (cy.back().op < 0) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing operator to carry");
-        }
+      for (auto& c : nd.carry) {  // the top carries only observables
+        const int gsite = nd.lo + c.first;
+        if (gsite < Blo) cy.push_back(rmc_carry{0, find_tag(A, gsite - Alo, c.second)});
+        else cy.push_back(rmc_carry{1, find_tag(B, gsite - Blo, c.second)});
+        if (cy.back().op < 0) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing operator to carry");
       }
       rmc_status st = rmc_couple(ctx, A, B, mt.data(), (int)mt.size(), top ? q : k, cy.data(), (int)cy.size(),
                                  top ? RMC_COUPLE_TOP : 0, &blk);
@@ -1935,7 +2027,7 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
     }
     owned.push_back(blk);
     if (!top) cache[nd.sig] = blk;
-    *out = blk;
+    *out = blk_of[id] = blk;
     return RMC_OK;
   };
   rmc_block* topb = nullptr;
@@ -1946,13 +2038,61 @@ extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, 
     ctx->err = e;
     return st;
   }
-  std::vector<double> E(std::min(q, topb->k));
+  const int qe = std::min(q, topb->k);
+  std::vector<double> E(qe);
   st = rmc_lowest(ctx, topb, q, E.data(), nullptr, nullptr);
-  for (int i = 0; i < q; ++i) E_out[i] = i < (int)E.size() ? E[i] : NAN;
+  for (int i = 0; i < q; ++i) E_out[i] = i < qe ? E[i] : NAN;
+  if (st == RMC_OK && n_obs > 0) {
+    // <psi_mu| O |psi_nu> = the carried operator in the top basis, q x q
+    std::vector<double> m((size_t)topb->k * topb->k);
+    for (int o = 0; o < n_obs && st == RMC_OK; ++o) {
+      const int j = find_tag(topb, observables[o].first, observables[o].second);
+      double* dst = obs_out + (size_t)o * q * q;
+      if (j < 0) { st = fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_states: observable not carried"); break; }
+      if (cudaMemcpy(m.data(), topb->ops + (size_t)j * topb->k * topb->k, sizeof(double) * m.size(),
+                     cudaMemcpyDeviceToHost) != cudaSuccess) {
+        st = fail(ctx, RMC_ERR_CUDA, "rmc_solve_chain_states: copy of an observable failed");
+        break;
+      }
+      for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b) dst[(size_t)a * q + b] = (a < qe && b < qe) ? m[(size_t)a * topb->k + b] : NAN;
+    }
+  }
+  if (st == RMC_OK && psi_out) {
+    Workspace ws(ctx);
+    double* psi = nullptr;
+    st = lift_block(ctx, ws, nodes, blk_of, 0, qe, &psi);
+    if (st == RMC_OK) {
+      const size_t len = (size_t)1 << n_sites;
+      if (cudaMemcpyAsync(psi_out, psi, sizeof(double) * qe * len, cudaMemcpyDeviceToHost, ctx->stream) !=
+              cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        st = fail(ctx, RMC_ERR_CUDA, "rmc_solve_chain_states: copy of the states failed");
+      for (size_t i = (size_t)qe * len; i < (size_t)q * len; ++i) psi_out[i] = NAN;
+    }
+  }
   cleanup();
   if (st != RMC_OK) return st;
   if (soft != RMC_OK) return fail(ctx, soft, "rmc_solve_chain: a merge did not converge");
   return RMC_OK;
+}
+
+}  // namespace
+
+extern "C" rmc_status rmc_solve_chain(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int n_onsite,
+                                      const int* onsite_site, const char* onsite_pauli, const double* onsite_coef,
+                                      int n_bonds, const int* bond_i, const int* bond_j, const char* bond_pauli_i,
+                                      const char* bond_pauli_j, const double* bond_coef, double* E_out) {
+  return solve_chain_core(ctx, n_sites, L0, k, q, n_onsite, onsite_site, onsite_pauli, onsite_coef, n_bonds, bond_i,
+                          bond_j, bond_pauli_i, bond_pauli_j, bond_coef, 0, nullptr, E_out, nullptr, nullptr);
+}
+
+extern "C" rmc_status rmc_solve_chain_states(rmc_ctx* ctx, const rmc_chain* c, int n_obs, const rmc_op_tag* obs,
+                                             double* E_out, double* obs_out, double* psi_out) {
+  if (!ctx) return RMC_ERR_INVAL;
+  if (!c) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_states: no chain");
+  return solve_chain_core(ctx, c->n_sites, c->L0, c->k, c->q, c->n_onsite, c->onsite_site, c->onsite_pauli,
+                          c->onsite_coef, c->n_bonds, c->bond_i, c->bond_j, c->bond_pauli_i, c->bond_pauli_j,
+                          c->bond_coef, n_obs, obs, E_out, obs_out, psi_out);
 }
 
 // ---------------------------------------------------------------------------
