@@ -324,7 +324,9 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
 
 /* The Chebyshev filter of one subspace iteration (Zhou and Saad's scaled
  * three-term recurrence on the H_eff of Eq. (7), the operator arguments as in
- * rmc_kron_matvec with dtype 0 = FP64 or 1 = FP32):
+ * rmc_kron_matvec with dtype 0 = FP64, 1 = FP32, or 3 = FP64 data with the
+ * products in double-FP32 arithmetic on the FP32 pipe (single-launch form
+ * only; ~1e-13 relative, the form the mixed paths refine with)):
  *   Y[v] = p(H) X[v] / ||p(H) X[v]||,   p = T_deg((H - c) / e) / T_deg((theta0 - c) / e),
  * e = (ub - a) / 2, c = (ub + a) / 2: the polynomial damps [a, ub] (bounded by
  * 1 / |T_deg((theta0 - c) / e)| there) and grows below a; theta0 < a < ub

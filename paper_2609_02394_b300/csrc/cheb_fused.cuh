@@ -198,4 +198,177 @@ __global__ void __launch_bounds__(kFusedThreads)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The same fused filter for FP64 data in double-FP32 arithmetic, for the FP64
+// refinement of the mixed paths.  This part's FP64 pipe issues ~1.9 DFMA per
+// clock per SM against 128 FP32 FMAs, so FP64-accurate products are formed on
+// the FP32 pipe instead: every value is an unevaluated sum hi + lo of two
+// floats (a "double-float", 48 significant bits), a product's rounding error
+// is recovered exactly with an FMA (Dekker's product, here in its FMA form)
+// and every addition into an accumulator keeps its error by Knuth's TwoSum, so
+// one multiply-add costs 12 FP32 instructions.  The lo*lo cross term is
+// dropped (2^-48 relative).  Sums over K <= 192 terms stay within ~1e-13
+// relative, against the 1e-8 residual target of the refinement.
+// Operators come pre-split (hi, lo) in global memory; the vectors and the
+// stage-1 intermediate are held split in shared memory; the recurrence's
+// epilogue and the final normalisation are evaluated in FP64 (a few
+// operations per element and step, against ~K multiply-adds).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 df_split(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ double df_value(float2 v) { return (double)v.x + (double)v.y; }
+
+// (s, t) += a * b  in double-float
+__device__ __forceinline__ void df_mac(float& s, float& t, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float u = s + p;
+  const float bp = u - s;
+  const float err = (s - (u - bp)) + (p - bp);
+  s = u;
+  t += err + e;
+}
+
+// cta_gemm in double-float: C(m, n) = sum_k A(m, k) B(k, n), operands float2.
+template <class Epi>
+__device__ __forceinline__ void cta_gemm_df(int M, int N, int K, const float2* A, int sam, int sak, const float2* B,
+                                            int sbk, int sbn, const Epi& epi) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int m0 = 0; m0 < M; m0 += 64) {
+    for (int n0 = 0; n0 < N; n0 += 64) {
+      int ar[4], bc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ar[i] = min(m0 + ty + 16 * i, M - 1) * sam;
+        bc[i] = min(n0 + tx + 16 * i, N - 1) * sbn;
+      }
+      float s[4][4], t[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[i][j] = t[i][j] = 0.f;
+      for (int k = 0; k < K; ++k) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = A[ar[i] + k * sak];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = B[k * sbk + bc[j]];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_mac(s[i][j], t[i][j], a[i], b[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n = n0 + tx + 16 * j;
+          if (n < N) epi(m, n, s[i][j], t[i][j]);
+        }
+      }
+    }
+  }
+}
+
+struct DfEpi1 {  // T[((j*kA + a)*nvl + v)*kB + b] = (s + t) renormalised
+  float2* Ts;
+  int kA, kB, nvl;
+  __device__ void operator()(int m, int n, float s, float t) const {
+    const int v = m / kA, a = m - v * kA, j = n / kB, b = n - j * kB;
+    const float hi = s + t;
+    Ts[((j * kA + a) * nvl + v) * kB + b] = make_float2(hi, t - (hi - s));
+  }
+};
+
+struct DfEpi2 {  // Yold <- alpha (acc + (EA[a] + EB[b]) x) + beta x + gamma z, in FP64
+  const float2* Ycur;
+  float2* Yold;
+  const double* EA;
+  const double* EB;
+  int kA, kB;
+  double alpha, beta, gamma;
+  __device__ void operator()(int a, int n, float s, float t) const {
+    const int v = n / kB, b = n - v * kB;
+    const int idx = (v * kA + a) * kB + b;
+    const double x = df_value(Ycur[idx]);
+    double y = alpha * ((double)s + (double)t + (EA[a] + EB[b]) * x) + beta * x;
+    if (gamma != 0.0) y += gamma * df_value(Yold[idx]);
+    Yold[idx] = df_split(y);
+  }
+};
+
+// Out = normalised p(H) X (deg >= 1, H X formed in the kernel) or Out = H X
+// (deg == 0), FP64 in and out, double-float inside.  Ahl (kA x n_ops kA) and
+// Bhl (n_ops kB x kB) are Acat and Bcat split into (hi, lo).  X and Out may
+// be the same array.
+__global__ void __launch_bounds__(kFusedThreads)
+    cheb_fused_df_kernel(const double* X, const double* __restrict__ EA, const double* __restrict__ EB,
+                         const float2* __restrict__ Ahl, const float2* __restrict__ Bhl, double* Out, FusedArgs p) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  float2* sm = reinterpret_cast<float2*>(fused_smem);
+  const int kA = p.kA, kB = p.kB, no = p.n_ops;
+  const int n = kA * kB;
+  const int v0 = blockIdx.x * p.vpc;
+  const int nvl = min(p.vpc, p.nv - v0);
+  if (nvl <= 0) return;
+  float2* Yp = sm;
+  float2* Yc = Yp + (size_t)p.vpc * n;
+  float2* Ts = Yc + (size_t)p.vpc * n;
+  double* red = reinterpret_cast<double*>(Ts + (size_t)no * p.vpc * n);
+  const long base = (long)v0 * n;
+  const int cnt = nvl * n;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) Yp[i] = df_split(X[base + i]);
+  __syncthreads();
+  auto product = [&](const float2* Ysrc, const DfEpi2& e2) {
+    if (no > 0) {
+      cta_gemm_df(nvl * kA, no * kB, kB, Ysrc, kB, 1, Bhl, 1, kB, DfEpi1{Ts, kA, kB, nvl});
+      __syncthreads();
+    }
+    cta_gemm_df(kA, nvl * kB, no * kA, Ahl, no * kA, 1, Ts, nvl * kB, 1, e2);
+    __syncthreads();
+  };
+  const double s1e = p.deg == 0 ? 1.0 : p.sigma1 / p.e;
+  const double b1 = p.deg == 0 ? 0.0 : -p.c * s1e;
+  product(Yp, DfEpi2{Yp, Yc, EA, EB, kA, kB, s1e, b1, 0.0});
+  double sigma = p.sigma1;
+  const double tau = 2.0 / p.sigma1;
+  for (int d = 2; d <= p.deg; ++d) {
+    const double s1 = 1.0 / (tau - sigma);
+    product(Yc, DfEpi2{Yc, Yp, EA, EB, kA, kB, 2 * s1 / p.e, -2 * s1 * p.c / p.e, -sigma * s1});
+    float2* t = Yp;
+    Yp = Yc;
+    Yc = t;
+    sigma = s1;
+  }
+  if (p.deg == 0) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) Out[base + i] = df_value(Yc[i]);
+    return;
+  }
+  for (int v = 0; v < nvl; ++v) {
+    const float2* y = Yc + (size_t)v * n;
+    double s = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double yi = df_value(y[i]);
+      s += yi * yi;
+    }
+    s = block_sum(s, red);
+    const double inv = s > 0 ? 1.0 / sqrt(s) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Out[base + (long)v * n + i] = df_value(y[i]) * inv;
+  }
+}
+
+// (hi, lo) split of an FP64 array
+__global__ void df_split_kernel(const double* __restrict__ in, long count, float2* __restrict__ out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    out[i] = df_split(in[i]);
+}
+
 }  // namespace rmc

@@ -409,6 +409,42 @@ rmc_status cheb_fused(rmc_ctx* ctx, const KronOp<T>& H, const T* X, const T* HX,
   return RMC_OK;
 }
 
+// The fused filter / product on FP64 data in double-FP32 arithmetic
+// (cheb_fused_df_kernel): deg >= 1 gives the normalised filter output with
+// H X formed in the kernel, deg == 0 the plain product.  *done = false when
+// the block does not fit (nothing launched).
+rmc_status cheb_fused_df(rmc_ctx* ctx, const KronOp<double>& H, const double* X, int nv, int deg, double theta0,
+                         double a, double ub, double* Out, bool* done) {
+  *done = false;
+  FusedArgs p;
+  size_t smem;
+  if (!fused_plan<double>(H, nv, &p, &smem)) return RMC_OK;  // same shared-memory layout size as FP64
+  Workspace ws(ctx);
+  const int no = H.n_ops;
+  float2 *Ahl = nullptr, *Bhl = nullptr;
+  if (no > 0) {
+    TRY(ws.get(&Ahl, (size_t)H.kA * no * H.kA));
+    TRY(ws.get(&Bhl, (size_t)no * H.kB * H.kB));
+    df_split_kernel<<<grid1d((long)H.kA * no * H.kA), 256, 0, ctx->stream>>>(H.Acat, (long)H.kA * no * H.kA, Ahl);
+    CKL();
+    df_split_kernel<<<grid1d((long)no * H.kB * H.kB), 256, 0, ctx->stream>>>(H.Bcat, (long)no * H.kB * H.kB, Bhl);
+    CKL();
+  }
+  p.deg = std::max(0, deg);
+  p.compute_hx = 1;
+  if (p.deg > 0) {
+    p.e = (ub - a) / 2;
+    p.c = (ub + a) / 2;
+    p.sigma1 = p.e / (theta0 - p.c);
+  }
+  ProfScope ps(ctx, 1, nv * (double)std::max(1, p.deg) * kron_flops_per_vector(H.kA, H.kB, no));
+  CK(cudaFuncSetAttribute(cheb_fused_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit));
+  cheb_fused_df_kernel<<<ceil_div(p.nv, p.vpc), kFusedThreads, smem, ctx->stream>>>(X, H.EA, H.EB, Ahl, Bhl, Out, p);
+  CKL();
+  *done = true;
+  return RMC_OK;
+}
+
 // Y = H X: the fused single-launch product when the block fits, else the
 // two-stage product (tensor cores for the TF32 working precision).
 template <typename T>
@@ -1220,7 +1256,7 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
         int deg = (int)std::floor(std::acosh(1e6) / std::acosh(std::max(x0, 1.0 + 1e-12)));
         deg = std::max(2, std::min(16, deg));
         bool fused = false;
-        TRY(cheb_fused<double>(ctx, H64, X64, nullptr, bf, deg, th_cur[0], a, ub, X64, &fused));
+        TRY(cheb_fused_df(ctx, H64, X64, bf, deg, th_cur[0], a, ub, X64, &fused));
         if (!fused) {
           Workspace wp(ctx);
           double *Y0, *Y1, *Y2, *Yout = nullptr;
@@ -1236,7 +1272,11 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
       }
     }
     TRY(cholqr64_refine(ctx, ws, X64, bf, n, tmp64));
-    TRY(kron_product<double>(ctx, H64, X64, bf, HX64, Tb64));
+    {
+      bool done = false;  // the mixed paths form the FP64-accurate product in double-FP32
+      if (refine) TRY(cheb_fused_df(ctx, H64, X64, bf, 0, 0.0, 0.0, 0.0, HX64, &done));
+      if (!done) TRY(kron_product<double>(ctx, H64, X64, bf, HX64, Tb64));
+    }
     TRY(gram<double>(ctx, ws, X64, bf, HX64, bf, n, Gs, true));
     TRY(syev64(ctx, ws, Gs, bf, w, Zs, chunked));
     TRY(combine<double>(ctx, Zs, true, bf, bf, X64, n, C, 1.0, 0.0, nullptr));
@@ -1657,7 +1697,8 @@ rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
                            double theta0, double a, double ub, int fused, void* Y) {
   TRY(check_ctx(ctx));
   if (kA < 1 || kB < 1 || n_ops < 0 || n_ops > kMaxOps || nv < 1 || !EA || !EB || !X || !Y ||
-      (n_ops && (!A || !B || !coef)) || dtype < 0 || dtype > 1 || deg < 0 || deg > 64 || (fused != 0 && fused != 1))
+      (n_ops && (!A || !B || !coef)) || dtype < 0 || dtype > 3 || dtype == 2 || deg < 0 || deg > 64 ||
+      (fused != 0 && fused != 1) || (dtype == 3 && !fused))
     return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: bad arguments");
   if (deg > 0 && !(theta0 < a && a < ub)) return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: need theta0 < a < ub");
   Workspace ws(ctx);
@@ -1680,6 +1721,15 @@ rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
       CKL();
     }
     H.Acat = Acat;
+    if constexpr (sizeof(T) == 8) {
+      if (dtype == 3) {
+        bool done = false;
+        TRY(cheb_fused_df(ctx, H, (const double*)X, nv, deg, theta0, a, ub, (double*)Y, &done));
+        if (!done)
+          return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: a %d x %d vector does not fit the fused kernel", kA, kB);
+        return RMC_OK;
+      }
+    }
     if (fused) {
       FusedArgs p;
       size_t smem;
@@ -1716,7 +1766,7 @@ rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
     CKL();
     return RMC_OK;
   };
-  return dtype == 0 ? run(double{}) : run(float{});
+  return (dtype == 0 || dtype == 3) ? run(double{}) : run(float{});
 }
 
 rmc_status rmc_syev(rmc_ctx* ctx, int m, const double* S, double* w, double* V) {

@@ -89,13 +89,16 @@ FILTER_CASES = [(16, 16, 3, 40, 8), (64, 64, 3, 9, 6), (24, 40, 1, 7, 5), (7, 13
 
 
 @pytest.mark.parametrize("kA,kB,n_ops,nv,deg", FILTER_CASES)
-@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("dtype", [0, 1, 3])
 @pytest.mark.parametrize("fused", [True, False])
 def test_chebyshev_filter_matches_dense_recurrence(ctx, kA, kB, n_ops, nv, deg, dtype, fused):
     """Both forms of the filter against the recurrence on the dense H_eff:
     damped interval [theta_m, ub] from the exact spectrum, scaled at its lowest
     eigenvalue; ragged shapes, several vectors per CTA, no coupling, degrees
-    0 (plain product), 1 and up to 12."""
+    0 (plain product), 1 and up to 12.  dtype 3 (FP64 data, double-FP32
+    products, single-launch form only) is held to 5e-12."""
+    if dtype == 3 and not fused:
+        pytest.skip("double-FP32 arithmetic exists in the single-launch form only")
     rng = np.random.default_rng(kA * 7919 + kB * 31 + n_ops * 7 + nv + deg)
     EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
     H = O.effective_hamiltonian(EA, EB, [(coef[j], oA[j], oB[j]) for j in range(n_ops)])
@@ -104,7 +107,7 @@ def test_chebyshev_filter_matches_dense_recurrence(ctx, kA, kB, n_ops, nv, deg, 
     theta0, a, ub = lam[0] - 1e-3, lam[m] + 1e-3, lam[-1] + 0.1
     X = rng.standard_normal((nv, kA, kB))
     ref = _dense_filter(H, X, deg, theta0, a, ub)
-    npdt = np.float64 if dtype == 0 else np.float32
+    npdt = np.float32 if dtype == 1 else np.float64
     d = [dev(v, npdt) for v in (EA, EB, oA, oB, X)]
     Y = dev(np.zeros_like(X), npdt)
     torch_cuda().cuda.synchronize()
@@ -112,7 +115,7 @@ def test_chebyshev_filter_matches_dense_recurrence(ctx, kA, kB, n_ops, nv, deg, 
                     coef, d[4].data_ptr(), deg, theta0, a, ub, fused, Y.data_ptr())
     got = host(Y)
     scale = max(1.0, np.abs(ref).max())
-    tol = 1e-11 if dtype == 0 else 2e-4
+    tol = {0: 1e-11, 1: 2e-4, 3: 5e-12}[dtype]
     assert np.abs(got - ref).max() <= tol * scale, np.abs(got - ref).max() / scale
 
 
