@@ -216,24 +216,6 @@ __global__ void __launch_bounds__(kFusedThreads)
 // operations per element and step, against ~K multiply-adds).
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float2 df_split(double v) {
-  const float hi = (float)v;
-  return make_float2(hi, (float)(v - (double)hi));
-}
-__device__ __forceinline__ double df_value(float2 v) { return (double)v.x + (double)v.y; }
-
-// (s, t) += a * b  in double-float
-__device__ __forceinline__ void df_mac(float& s, float& t, float2 a, float2 b) {
-  const float p = a.x * b.x;
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  const float u = s + p;
-  const float bp = u - s;
-  const float err = (s - (u - bp)) + (p - bp);
-  s = u;
-  t += err + e;
-}
 
 // cta_gemm in double-float: C(m, n) = sum_k A(m, k) B(k, n), operands float2.
 template <class Epi>

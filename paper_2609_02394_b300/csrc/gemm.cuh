@@ -11,6 +11,8 @@
 // filled, so any M, N, K (ragged tails included) is valid.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace rmc {
@@ -23,15 +25,20 @@ struct GemmShape {
   const int* skip = nullptr;  // if non-null and *skip != 0 the launch does nothing
 };
 
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB, class Epi>
+// With DF (T = double only) the tiles are held as (hi, lo) float pairs and
+// the products are accumulated in double-float arithmetic on the FP32 pipe
+// (see common.cuh); the epilogue receives hi + lo as a double.
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB, class Epi, bool DF = false>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, GemmShape s, Epi epi) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int RY = BM / TM;  // thread rows
   constexpr int RX = BN / TN;  // thread cols
+  static_assert(!DF || sizeof(T) == 8, "double-float products take FP64 data");
+  using ST = std::conditional_t<DF, float2, T>;
   if (s.skip && *s.skip) return;
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  __shared__ ST As[BK][BM + 1];
+  __shared__ ST Bs[BK][BN + 1];
 
   const int batch = blockIdx.z / s.k_splits;
   const int split = blockIdx.z % s.k_splits;
@@ -44,11 +51,12 @@ gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, GemmShape s, Epi e
 
   const int tid = threadIdx.x;
   const int ty = tid / RX, tx = tid % RX;
-  T acc[TM][TN];
+  using AT = std::conditional_t<DF, float, T>;
+  AT acc[TM][TN], acc_lo[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = acc_lo[i][j] = AT(0);
 
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
     // A tile: BM x BK
@@ -59,7 +67,8 @@ gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, GemmShape s, Epi e
       const int gm = m0 + mm, gk = k0 + kk;
       T v = T(0);
       if (gm < s.M && gk < kend) v = TA ? A[(long)gk * s.lda + gm] : A[(long)gm * s.lda + gk];
-      As[kk][mm] = v;
+      if constexpr (DF) As[kk][mm] = df_split(v);
+      else As[kk][mm] = v;
     }
     // B tile: BK x BN
 #pragma unroll
@@ -69,12 +78,13 @@ gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, GemmShape s, Epi e
       const int gn = n0 + nn, gk = k0 + kk;
       T v = T(0);
       if (gn < s.N && gk < kend) v = TB ? B[(long)gn * s.ldb + gk] : B[(long)gk * s.ldb + gn];
-      Bs[kk][nn] = v;
+      if constexpr (DF) Bs[kk][nn] = df_split(v);
+      else Bs[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[TM], b[TN];
+      ST a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * RY];
 #pragma unroll
@@ -82,7 +92,10 @@ gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, GemmShape s, Epi e
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) {
+          if constexpr (DF) df_mac(acc[i][j], acc_lo[i][j], a[i], b[j]);
+          else acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
     }
     __syncthreads();
   }
@@ -93,7 +106,9 @@ gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, GemmShape s, Epi e
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + j * RX;
-      if (gn < s.N) epi(batch, split, gm, gn, acc[i][j]);
+      if (gn >= s.N) continue;
+      if constexpr (DF) epi(batch, split, gm, gn, (T)((double)acc[i][j] + (double)acc_lo[i][j]));
+      else epi(batch, split, gm, gn, acc[i][j]);
     }
   }
 }
@@ -135,11 +150,11 @@ __global__ void reduce_splits_kernel(const T* __restrict__ P, int splits, long s
 
 // Launch helper.  Tile presets: FP32 64x64x16 / 4x4, FP64 64x64x8 / 4x4,
 // small 32x32 / 2x2 (for the b x b products of the Rayleigh-Ritz steps).
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB, class Epi>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB, class Epi, bool DF = false>
 inline void launch_gemm(const T* A, const T* B, const GemmShape& s, int batches, const Epi& epi,
                         cudaStream_t st) {
   dim3 grid(ceil_div(s.N, BN), ceil_div(s.M, BM), batches * s.k_splits);
-  gemm_kernel<T, BM, BN, BK, TM, TN, TA, TB, Epi><<<grid, (BM / TM) * (BN / TN), 0, st>>>(A, B, s, epi);
+  gemm_kernel<T, BM, BN, BK, TM, TN, TA, TB, Epi, DF><<<grid, (BM / TM) * (BN / TN), 0, st>>>(A, B, s, epi);
 }
 
 }  // namespace rmc

@@ -215,6 +215,15 @@ template <typename T, bool TA, bool TB, class Epi>
 void gemm_small(const T* A, const T* B, const GemmShape& s, int batches, const Epi& epi, cudaStream_t st) {
   launch_gemm<T, 16, 16, 16, 1, 1, TA, TB>(A, B, s, batches, epi, st);
 }
+// FP64 data, double-float products on the FP32 pipe (64 x 64 x 8 tiles)
+template <bool TA, bool TB, class Epi>
+void gemm_df(const double* A, const double* B, const GemmShape& s, int batches, const Epi& epi, cudaStream_t st) {
+  launch_gemm<double, 64, 64, 8, 4, 4, TA, TB, Epi, true>(A, B, s, batches, epi, st);
+}
+// The mixed paths form their FP64-accurate block products (Gram matrices and
+// basis combinations of the refinement and the rotations) in double-float;
+// the FP64 path keeps native FP64.
+inline bool fp64_by_df(const rmc_ctx* ctx) { return ctx->cfg.precision != RMC_PREC_FP64; }
 
 // G (nv1 x nv2) = X1 X2^T, contraction over n, deterministic split-K.
 template <typename T>
@@ -228,6 +237,16 @@ rmc_status gram(rmc_ctx* ctx, Workspace& ws, const T* X1, int nv1, const T* X2, 
   TRY(ws.get(&P, (size_t)splits * nv1 * nv2));
   GemmShape s{nv1, nv2, (int)n, n, n, 0, 0, splits};
   EpiStore<T> epi{P, nv2, 0, (long)nv1 * nv2, T(1), T(0)};
+  if constexpr (sizeof(T) == 8) {
+    if (fp64_by_df(ctx)) {
+      gemm_df<false, true>(X1, X2, s, 1, epi, ctx->stream);
+      CKL();
+      reduce_splits_kernel<T><<<grid1d((long)nv1 * nv2), 256, 0, ctx->stream>>>(
+          P, splits, (long)nv1 * nv2, nv1, nv2, G, nv2, T(1), T(0), symmetrize ? 1 : 0);
+      CKL();
+      return RMC_OK;
+    }
+  }
   if (nv1 <= 32 && nv2 <= 32) gemm_small<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
   else gemm_big<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
   CKL();
@@ -245,6 +264,14 @@ rmc_status combine(rmc_ctx* ctx, const T* W, bool transW, int nvo, int nvi, cons
   ProfScope ps(ctx, 5, 2.0 * nvo * nvi * (double)n);
   GemmShape s{nvo, (int)n, nvi, transW ? nvo : nvi, n, 0, 0, 1};
   EpiAxpby<T> epi{Out, Src, n, n, 0, 0, alpha, beta};
+  if constexpr (sizeof(T) == 8) {
+    if (fp64_by_df(ctx)) {
+      if (transW) gemm_df<true, false>(W, X, s, 1, epi, ctx->stream);
+      else gemm_df<false, false>(W, X, s, 1, epi, ctx->stream);
+      CKL();
+      return RMC_OK;
+    }
+  }
   if (transW) gemm_big<T, true, false>(W, X, s, 1, epi, ctx->stream);
   else gemm_big<T, false, false>(W, X, s, 1, epi, ctx->stream);
   CKL();
