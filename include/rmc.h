@@ -78,6 +78,10 @@ typedef struct rmc_config {
   int guard;               /* extra vectors beyond the retained count; <= 0:
                               max(16, k_ret / 2), capped by the dimension       */
   double tau_deg;          /* degenerate-cut threshold; <= 0: 1e-7              */
+  int lanes;               /* merges of one level that rmc_solve_chain and
+                              rmc_couple_batch run at once, each on its own
+                              stream and host thread; <= 0: up to 8; 1: one
+                              at a time (the solve server's slots use 1)        */
 } rmc_config;
 
 typedef struct rmc_ctx rmc_ctx;
@@ -181,6 +185,31 @@ rmc_status rmc_couple(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B,
                       const rmc_term* terms, int n_terms, int k_keep,
                       const rmc_carry* carry, int n_carry, int flags,
                       rmc_block** out);
+
+/* One merge of a batch: the arguments of rmc_couple. */
+typedef struct rmc_couple_desc {
+  const rmc_block* A;
+  const rmc_block* B;
+  const rmc_term* terms;
+  int n_terms;
+  int k_keep;
+  const rmc_carry* carry;
+  int n_carry;
+  int flags;
+} rmc_couple_desc;
+
+/* n independent merges (for instance every merge of one level of the
+ * recursion, Algorithm 1, for one chain or many) run at once: up to
+ * cfg.lanes of them concurrently, each on its own CUDA stream and host thread
+ * inside the context, sharing its memory pool and budget.  out[i] and
+ * status[i] receive each merge's block and status as rmc_couple would return
+ * them (out[i] is NULL unless status[i] is RMC_OK or RMC_ERR_NOCONV); the
+ * blocks belong to ctx.  The inputs must not be freed while the call runs; the
+ * call synchronises before returning, and returns the first failing status
+ * (hard errors before RMC_ERR_NOCONV) with that merge's message in
+ * rmc_last_error. */
+rmc_status rmc_couple_batch(rmc_ctx* ctx, int n, const rmc_couple_desc* descs,
+                            rmc_block** out, rmc_status* status);
 
 /* Lowest q energies of a block (Algorithm 1, last step), ascending, into the
  * host array E_out[q]; q is clipped to the block's kept count, which is

@@ -30,6 +30,7 @@ EXPORTED = [
     "rmc_kron_matvec_noalloc", "rmc_server_create", "rmc_server_destroy", "rmc_submit", "rmc_poll",
     "rmc_server_stats", "rmc_estimate_bytes", "rmc_solve_chains", "rmc_server_profile",
     "rmc_server_profile_read", "rmc_server_last_error", "rmc_cheb_filter", "rmc_solve_chain_states",
+    "rmc_couple_batch",
 ]
 PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
@@ -43,7 +44,7 @@ class RmcError(RuntimeError):
 class rmc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
                 ("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("guard", ctypes.c_int), ("tau_deg", ctypes.c_double)]
+                ("guard", ctypes.c_int), ("tau_deg", ctypes.c_double), ("lanes", ctypes.c_int)]
 
 
 class rmc_op_tag(ctypes.Structure):
@@ -56,6 +57,12 @@ class rmc_term(ctypes.Structure):
 
 class rmc_carry(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int), ("op", ctypes.c_int)]
+
+
+class rmc_couple_desc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("terms", ctypes.POINTER(rmc_term)),
+                ("n_terms", ctypes.c_int), ("k_keep", ctypes.c_int), ("carry", ctypes.POINTER(rmc_carry)),
+                ("n_carry", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class rmc_chain(ctypes.Structure):
@@ -132,6 +139,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_profile_read": ([vp, ip, P(ctypes.c_uint64), P(ctypes.c_uint64), P(dp), P(dp)], ip),
         "rmc_cheb_filter": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, ip, dp, dp, dp, ip, vp], ip),
         "rmc_solve_chain_states": ([vp, P(rmc_chain), ip, P(rmc_op_tag), P(dp), P(dp), P(dp)], ip),
+        "rmc_couple_batch": ([vp, ip, P(rmc_couple_desc), P(vp), P(ip)], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -198,10 +206,11 @@ class Context:
     """One solver context (device, stream, memory budget, precision)."""
 
     def __init__(self, device: int = 0, precision: str = "fp64", stream: Optional[int] = None,
-                 mem_budget: int = 0, tol: float = 0.0, max_iter: int = 0, guard: int = 0, tau_deg: float = 0.0):
+                 mem_budget: int = 0, tol: float = 0.0, max_iter: int = 0, guard: int = 0, tau_deg: float = 0.0,
+                 lanes: int = 0):
         self.lib = load_library()
         cfg = rmc_config(device, ctypes.c_void_p(stream) if stream else None, mem_budget, PRECISIONS[precision],
-                         tol, max_iter, guard, tau_deg)
+                         tol, max_iter, guard, tau_deg, lanes)
         h = ctypes.c_void_p()
         st = self.lib.rmc_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != RMC_OK:
@@ -297,6 +306,27 @@ class Context:
         self._check(st, allow=(RMC_ERR_NOCONV,) if allow_noconv else ())
         return Block(self, out.value)
 
+    def couple_batch(self, merges, allow_noconv: bool = False):
+        """Independent merges at once: ``merges`` is a list of (A, B, terms,
+        k_keep, carry, top) tuples as for ``couple``; returns their blocks."""
+        n = len(merges)
+        keep = []
+        descs = (rmc_couple_desc * max(1, n))()
+        for i, (A, B, terms, k_keep, carry, top) in enumerate(merges):
+            tt = (rmc_term * max(1, len(terms)))(*[rmc_term(c, a, b) for c, a, b in terms])
+            cc = (rmc_carry * max(1, len(carry)))(*[rmc_carry(s_, o) for s_, o in carry])
+            keep += [tt, cc]
+            descs[i] = rmc_couple_desc(A.handle, B.handle, ctypes.cast(tt, ctypes.POINTER(rmc_term)), len(terms),
+                                       k_keep, ctypes.cast(cc, ctypes.POINTER(rmc_carry)), len(carry),
+                                       RMC_COUPLE_TOP if top else 0)
+        outs = (ctypes.c_void_p * max(1, n))()
+        sts = (ctypes.c_int * max(1, n))()
+        st = self.lib.rmc_couple_batch(self.h, n, descs, outs, sts)
+        del keep
+        blocks = [Block(self, outs[i]) if outs[i] else None for i in range(n)]
+        self._check(st, allow=(RMC_ERR_NOCONV,) if allow_noconv else ())
+        return blocks
+
     def lowest(self, blk: Block, q: int, with_states: bool = False):
         k, _, rows, _ = blk.info()
         qq = min(q, k)
@@ -376,7 +406,7 @@ class Context:
 
 
 def _config(device=0, precision="mixed", mem_budget=0, tol=0.0, max_iter=0, guard=0, tau_deg=0.0):
-    return rmc_config(device, None, mem_budget, PRECISIONS[precision], tol, max_iter, guard, tau_deg)
+    return rmc_config(device, None, mem_budget, PRECISIONS[precision], tol, max_iter, guard, tau_deg, 1)
 
 
 def solve_chains(chains, slots: int = 8, **cfg):

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -25,6 +26,7 @@
 #include <set>
 #include <string>
 #include <tuple>
+#include <thread>
 #include <vector>
 
 #include "../../include/rmc.h"
@@ -53,9 +55,16 @@ struct rmc_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaMemPool_t pool = nullptr;
+  bool own_pool = true;
   size_t budget = 0;
   size_t in_use = 0;
   std::map<void*, size_t> live;
+  // lanes: child contexts that run merges of one level concurrently
+  // (rmc_couple_batch); each has its own stream, status words and pinned
+  // staging, shares this context's pool, and charges its bytes to `acct`
+  rmc_ctx* acct = nullptr;  // context whose budget this one draws on (null: itself)
+  std::mutex acct_mu;       // guards in_use of an accounting context
+  std::vector<rmc_ctx*> lanes;
   rmc_config cfg{};
   std::string err;
   uint64_t launches = 0, iterations = 0;
@@ -109,15 +118,21 @@ rmc_status fail(rmc_ctx* ctx, rmc_status st, const char* fmt, ...) {
 
 rmc_status dalloc(rmc_ctx* ctx, void** p, size_t bytes) {
   bytes = std::max<size_t>(bytes, 256);
-  if (ctx->in_use + bytes > ctx->budget)
-    return fail(ctx, RMC_ERR_NOMEM, "device-memory budget exceeded: need %zu more bytes, %zu of %zu in use",
-                bytes, ctx->in_use, ctx->budget);
+  rmc_ctx* a = ctx->acct ? ctx->acct : ctx;
+  {
+    std::lock_guard<std::mutex> lk(a->acct_mu);
+    if (a->in_use + bytes > a->budget)
+      return fail(ctx, RMC_ERR_NOMEM, "device-memory budget exceeded: need %zu more bytes, %zu of %zu in use",
+                  bytes, a->in_use, a->budget);
+    a->in_use += bytes;
+  }
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    std::lock_guard<std::mutex> lk(a->acct_mu);
+    a->in_use -= bytes;
     return fail(ctx, RMC_ERR_NOMEM, "cudaMallocFromPoolAsync(%zu): %s", bytes, cudaGetErrorString(e));
   }
-  ctx->in_use += bytes;
   ctx->live[*p] = bytes;
   return RMC_OK;
 }
@@ -126,7 +141,9 @@ void dfree(rmc_ctx* ctx, void* p) {
   if (!p) return;
   auto it = ctx->live.find(p);
   if (it != ctx->live.end()) {
-    ctx->in_use -= it->second;
+    rmc_ctx* a = ctx->acct ? ctx->acct : ctx;
+    std::lock_guard<std::mutex> lk(a->acct_mu);
+    a->in_use -= it->second;
     ctx->live.erase(it);
   }
   cudaFreeAsync(p, ctx->stream);
@@ -1382,6 +1399,35 @@ rmc_status check_ctx(rmc_ctx* ctx) {
 
 }  // namespace
 
+// Lanes of a context (see rmc_ctx): created on first use, kept until the
+// context is destroyed.
+constexpr int kMaxLanes = 8;
+
+rmc_status ensure_lanes(rmc_ctx* ctx, int L) {
+  while ((int)ctx->lanes.size() < L) {
+    std::unique_ptr<rmc_ctx> c(new rmc_ctx);
+    rmc_ctx* lc = c.get();
+    lc->device = ctx->device;
+    lc->cfg = ctx->cfg;
+    lc->cfg.stream = nullptr;
+    lc->trace = ctx->trace;
+    lc->budget = ctx->budget;
+    lc->acct = ctx->acct ? ctx->acct : ctx;
+    lc->pool = ctx->pool;
+    lc->own_pool = false;
+    {
+      rmc_ctx* ctx = lc;  // the checks below report on the lane
+      CK(cudaStreamCreateWithFlags(&lc->stream, cudaStreamNonBlocking));
+      lc->own_stream = true;
+      CK(cudaMalloc(&lc->d_status, 64 * sizeof(int)));
+      CK(cudaMemset(lc->d_status, 0, 64 * sizeof(int)));
+      CK(cudaMallocHost(&lc->h_pinned, kPinnedDoubles * sizeof(double)));
+    }
+    ctx->lanes.push_back(c.release());
+  }
+  return RMC_OK;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1427,12 +1473,14 @@ rmc_status rmc_create(rmc_ctx** out, const rmc_config* cfg_in) {
 rmc_status rmc_destroy(rmc_ctx* ctx) {
   if (!ctx) return RMC_ERR_INVAL;
   cudaSetDevice(ctx->device);
+  for (rmc_ctx* l : ctx->lanes) rmc_destroy(l);
+  ctx->lanes.clear();
   std::vector<rmc_block*> bl(ctx->blocks.begin(), ctx->blocks.end());
   for (rmc_block* b : bl) free_block(ctx, b);
   cudaStreamSynchronize(ctx->stream);
   harvest(ctx);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  if (ctx->pool && ctx->own_pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1441,7 +1489,7 @@ rmc_status rmc_destroy(rmc_ctx* ctx) {
 }
 
 const char* rmc_last_error(const rmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-size_t rmc_mem_in_use(const rmc_ctx* ctx) { return ctx ? ctx->in_use : 0; }
+size_t rmc_mem_in_use(const rmc_ctx* ctx) { return ctx ? ctx->in_use : 0; }  // lanes charge their parent
 void* rmc_stream(const rmc_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 rmc_status rmc_stats(const rmc_ctx* ctx, uint64_t* launches, uint64_t* iterations) {
@@ -1608,6 +1656,101 @@ rmc_status rmc_couple(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B, cons
   harvest(ctx);
   if (e != cudaSuccess) return fail(ctx, RMC_ERR_CUDA, "rmc_couple: %s", cudaGetErrorString(e));
   return soft;
+}
+
+rmc_status rmc_couple_batch(rmc_ctx* ctx, int n, const rmc_couple_desc* d, rmc_block** out, rmc_status* status) {
+  TRY(check_ctx(ctx));
+  if (n < 0 || (n > 0 && (!d || !out || !status)))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_couple_batch: bad arguments");
+  for (int i = 0; i < n; ++i) {
+    out[i] = nullptr;
+    status[i] = RMC_OK;
+  }
+  if (n == 0) return RMC_OK;
+  const int want = ctx->cfg.lanes > 0 ? ctx->cfg.lanes : kMaxLanes;
+  const int L = std::min(n, std::min(want, kMaxLanes));
+  if (L <= 1) {  // one at a time on this context
+    rmc_status first = RMC_OK;
+    std::string msg;
+    for (int i = 0; i < n; ++i) {
+      status[i] = rmc_couple(ctx, d[i].A, d[i].B, d[i].terms, d[i].n_terms, d[i].k_keep, d[i].carry, d[i].n_carry,
+                             d[i].flags, &out[i]);
+      if (status[i] != RMC_OK && status[i] != RMC_ERR_NOCONV) out[i] = nullptr;
+      const bool hard = status[i] != RMC_OK && status[i] != RMC_ERR_NOCONV;
+      if ((hard && (first == RMC_OK || first == RMC_ERR_NOCONV)) || (status[i] == RMC_ERR_NOCONV && first == RMC_OK)) {
+        first = status[i];
+        msg = ctx->err;
+      }
+    }
+    if (first != RMC_OK) ctx->err = "rmc_couple_batch: " + msg;
+    return first;
+  }
+  TRY(ensure_lanes(ctx, L));
+  // the lanes start after everything queued on this context's stream
+  cudaEvent_t ready;
+  CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  CK(cudaEventRecord(ready, ctx->stream));
+  for (int l = 0; l < L; ++l) {
+    ctx->lanes[l]->prof = ctx->prof;
+    CK(cudaStreamWaitEvent(ctx->lanes[l]->stream, ready, 0));
+  }
+  std::atomic<int> next{0};
+  std::vector<int> lane_of(n, -1);
+  std::vector<std::string> msgs(n);
+  std::vector<std::thread> th;
+  for (int l = 0; l < L; ++l) {
+    th.emplace_back([&, l]() {
+      rmc_ctx* lc = ctx->lanes[l];
+      for (int i = next++; i < n; i = next++) {
+        lane_of[i] = l;
+        status[i] = rmc_couple(lc, d[i].A, d[i].B, d[i].terms, d[i].n_terms, d[i].k_keep, d[i].carry,
+                               d[i].n_carry, d[i].flags, &out[i]);
+        if (status[i] != RMC_OK) msgs[i] = lc->err;  // the lane's next call clears it
+        if (status[i] != RMC_OK && status[i] != RMC_ERR_NOCONV) out[i] = nullptr;
+      }
+    });
+  }
+  for (auto& t : th) t.join();
+  cudaEventDestroy(ready);
+  // blocks pass to this context; counters and timings join its own
+  rmc_status first = RMC_OK;
+  std::string msg;
+  for (int i = 0; i < n; ++i) {
+    rmc_ctx* lc = ctx->lanes[lane_of[i]];
+    if (out[i]) {
+      lc->blocks.erase(out[i]);
+      ctx->blocks.insert(out[i]);
+      for (void* p : {(void*)out[i]->E, (void*)out[i]->ops, (void*)out[i]->basis}) {
+        auto it = p ? lc->live.find(p) : lc->live.end();
+        if (it != lc->live.end()) {
+          ctx->live[p] = it->second;
+          lc->live.erase(it);
+        }
+      }
+    }
+    const bool hard = status[i] != RMC_OK && status[i] != RMC_ERR_NOCONV;
+    if ((hard && (first == RMC_OK || first == RMC_ERR_NOCONV)) || (status[i] == RMC_ERR_NOCONV && first == RMC_OK)) {
+      first = status[i];
+      msg = msgs[i];
+    }
+  }
+  for (int l = 0; l < L; ++l) {
+    rmc_ctx* lc = ctx->lanes[l];
+    harvest(lc);
+    ctx->launches += lc->launches;
+    ctx->iterations += lc->iterations;
+    lc->launches = lc->iterations = 0;
+    for (int k = 0; k < RMC_PROF_KINDS; ++k) {
+      ctx->prof_groups[k] += lc->prof_groups[k];
+      ctx->prof_launches[k] += lc->prof_launches[k];
+      ctx->prof_ms[k] += lc->prof_ms[k];
+      ctx->prof_flops[k] += lc->prof_flops[k];
+      lc->prof_groups[k] = lc->prof_launches[k] = 0;
+      lc->prof_ms[k] = lc->prof_flops[k] = 0;
+    }
+  }
+  if (first != RMC_OK) ctx->err = "rmc_couple_batch: " + msg;
+  return first;
 }
 
 rmc_status rmc_lowest(rmc_ctx* ctx, const rmc_block* blk, int q, double* E_out, double* C_out, int* k_eff_out) {
@@ -2021,6 +2164,15 @@ rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int
   }
   for (ChainNode& nd : nodes) nd.carry.assign(need[nd.sig].begin(), need[nd.sig].end());
 
+  // Build level by level: the leaves, then every merge of one height as one
+  // batch (independent merges of Algorithm 1's recursion run at once on the
+  // context's lanes).  Blocks with equal signatures are built once.
+  std::vector<int> height(nodes.size(), 0);
+  std::function<int(int)> measure = [&](int id) -> int {
+    if (nodes[id].left < 0) return height[id] = 0;
+    return height[id] = 1 + std::max(measure(nodes[id].left), measure(nodes[id].right));
+  };
+  measure(0);
   std::map<std::string, rmc_block*> cache;
   std::vector<rmc_block*> owned;
   std::vector<rmc_block*> blk_of(nodes.size(), nullptr);
@@ -2028,60 +2180,65 @@ rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int
   auto cleanup = [&]() {
     for (rmc_block* b : owned) free_block(ctx, b);
   };
-  std::function<rmc_status(int, bool, rmc_block**)> build = [&](int id, bool top, rmc_block** out) -> rmc_status {
+  auto bail = [&](rmc_status st) {
+    std::string e = ctx->err;
+    cleanup();
+    ctx->err = e;
+    return st;
+  };
+  for (size_t id = 0; id < nodes.size(); ++id) {
     const ChainNode& nd = nodes[id];
+    if (nd.left >= 0) continue;
+    const bool top = id == 0;
     if (!top) {
       auto it = cache.find(nd.sig);
-      if (it != cache.end()) {
-        *out = blk_of[id] = it->second;
-        // the shared block's children serve this node's lifting too
-        if (nd.left >= 0) {
-          for (size_t o = 0; o < nodes.size(); ++o)
-            if (blk_of[o] == it->second && nodes[o].left >= 0 && (int)o != id) {
-              blk_of[nd.left] = blk_of[nodes[o].left];
-              blk_of[nd.right] = blk_of[nodes[o].right];
-              std::function<void(int, int)> copy_sub = [&](int dst, int src) {
-                blk_of[dst] = blk_of[src];
-                if (nodes[dst].left >= 0 && nodes[src].left >= 0) {
-                  copy_sub(nodes[dst].left, nodes[src].left);
-                  copy_sub(nodes[dst].right, nodes[src].right);
-                }
-              };
-              copy_sub(nd.left, nodes[o].left);
-              copy_sub(nd.right, nodes[o].right);
-              break;
-            }
-        }
-        return RMC_OK;
+      if (it != cache.end()) { blk_of[id] = it->second; continue; }
+    }
+    const int L = nd.hi - nd.lo;
+    std::vector<int> os, bi, bj;
+    std::vector<char> op, pi, pj;
+    std::vector<double> oc, bc;
+    for (const CTerm& t : terms) {
+      if (t.j < 0 && t.i >= nd.lo && t.i < nd.hi) { os.push_back(t.i - nd.lo); op.push_back(t.pi); oc.push_back(t.coef); }
+      if (t.j >= 0 && t.i >= nd.lo && t.j < nd.hi) {
+        bi.push_back(t.i - nd.lo); bj.push_back(t.j - nd.lo); pi.push_back(t.pi); pj.push_back(t.pj); bc.push_back(t.coef);
       }
     }
+    std::vector<rmc_op_tag> cr;
+    for (auto& c : nd.carry) cr.push_back(rmc_op_tag{c.first, c.second});
     rmc_block* blk = nullptr;
-    if (nd.left < 0) {
-      const int L = nd.hi - nd.lo;
-      std::vector<int> os, bi, bj;
-      std::vector<char> op, pi, pj;
-      std::vector<double> oc, bc;
-      for (const CTerm& t : terms) {
-        if (t.j < 0 && t.i >= nd.lo && t.i < nd.hi) { os.push_back(t.i - nd.lo); op.push_back(t.pi); oc.push_back(t.coef); }
-        if (t.j >= 0 && t.i >= nd.lo && t.j < nd.hi) {
-          bi.push_back(t.i - nd.lo); bj.push_back(t.j - nd.lo); pi.push_back(t.pi); pj.push_back(t.pj); bc.push_back(t.coef);
-        }
+    rmc_status st = rmc_build_leaf_pauli(ctx, L, (top || nd.sub) ? (1 << L) : k, (int)os.size(), os.data(), op.data(),
+                                         oc.data(), (int)bi.size(), bi.data(), bj.data(), pi.data(), pj.data(),
+                                         bc.data(), (int)cr.size(), cr.data(), &blk);
+    if (st != RMC_OK) return bail(st);
+    owned.push_back(blk);
+    if (!top) cache[nd.sig] = blk;
+    blk_of[id] = blk;
+  }
+  for (int h = 1; h <= height[0]; ++h) {
+    std::vector<int> ids, dup;
+    std::set<std::string> queued;
+    std::vector<std::vector<rmc_term>> mts;
+    std::vector<std::vector<rmc_carry>> cys;
+    std::vector<int> keeps, flags;
+    for (size_t id = 0; id < nodes.size(); ++id) {
+      const ChainNode& nd = nodes[id];
+      if (nd.left < 0 || height[id] != h) continue;
+      const bool top = id == 0;
+      if (!top) {
+        auto it = cache.find(nd.sig);
+        if (it != cache.end()) { blk_of[id] = it->second; continue; }
+        if (queued.count(nd.sig)) { dup.push_back((int)id); continue; }
+        queued.insert(nd.sig);
       }
-      std::vector<rmc_op_tag> cr;
-      for (auto& c : nd.carry) cr.push_back(rmc_op_tag{c.first, c.second});
-      TRY(rmc_build_leaf_pauli(ctx, L, (top || nd.sub) ? (1 << L) : k, (int)os.size(), os.data(), op.data(), oc.data(),
-                               (int)bi.size(), bi.data(), bj.data(), pi.data(), pj.data(), bc.data(), (int)cr.size(),
-                               cr.data(), &blk));
-    } else {
-      rmc_block *A = nullptr, *B = nullptr;
-      TRY(build(nd.left, false, &A));
-      TRY(build(nd.right, false, &B));
+      const rmc_block* A = blk_of[nd.left];
+      const rmc_block* B = blk_of[nd.right];
       const int Alo = nodes[nd.left].lo, Blo = nodes[nd.right].lo, Bhi = nodes[nd.right].hi;
       std::vector<rmc_term> mt;
       for (const CTerm& t : terms) {
         if (t.j < 0 || !(t.i >= Alo && t.i < Blo && t.j >= Blo && t.j < Bhi)) continue;
         const int oa = find_tag(A, t.i - Alo, t.pi), ob = find_tag(B, t.j - Blo, t.pj);
-        if (oa < 0 || ob < 0) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing carried operator");
+        if (oa < 0 || ob < 0) return bail(fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing carried operator"));
         // Y Y = -(iY)(iY): carried Y operators are iY
         mt.push_back(rmc_term{(t.pi == 'Y' && t.pj == 'Y') ? -t.coef : t.coef, oa, ob});
       }
@@ -2090,31 +2247,44 @@ rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int
         const int gsite = nd.lo + c.first;
         if (gsite < Blo) cy.push_back(rmc_carry{0, find_tag(A, gsite - Alo, c.second)});
         else cy.push_back(rmc_carry{1, find_tag(B, gsite - Blo, c.second)});
-        if (cy.back().op < 0) return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing operator to carry");
+        if (cy.back().op < 0)
+          return bail(fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing operator to carry"));
       }
-      rmc_status st = rmc_couple(ctx, A, B, mt.data(), (int)mt.size(), top ? q : k, cy.data(), (int)cy.size(),
-                                 top ? RMC_COUPLE_TOP : 0, &blk);
-      if (st == RMC_ERR_NOCONV) soft = st;
-      else if (st != RMC_OK) return st;
+      ids.push_back((int)id);
+      mts.push_back(std::move(mt));
+      cys.push_back(std::move(cy));
+      keeps.push_back(top ? q : k);
+      flags.push_back(top ? RMC_COUPLE_TOP : 0);
+    }
+    const int nb = (int)ids.size();
+    std::vector<rmc_couple_desc> descs(nb);
+    for (int b = 0; b < nb; ++b) {
+      const ChainNode& nd = nodes[ids[b]];
+      descs[b] = rmc_couple_desc{blk_of[nd.left], blk_of[nd.right], mts[b].data(), (int)mts[b].size(), keeps[b],
+                                 cys[b].data(), (int)cys[b].size(), flags[b]};
+    }
+    std::vector<rmc_block*> outs(nb, nullptr);
+    std::vector<rmc_status> sts(nb, RMC_OK);
+    const rmc_status st = rmc_couple_batch(ctx, nb, descs.data(), outs.data(), sts.data());
+    for (int b = 0; b < nb; ++b)
+      if (outs[b]) owned.push_back(outs[b]);
+    if (st != RMC_OK && st != RMC_ERR_NOCONV) return bail(st);
+    if (st == RMC_ERR_NOCONV) soft = st;
+    for (int b = 0; b < nb; ++b) {
+      const ChainNode& nd = nodes[ids[b]];
+      rmc_block* blk = outs[b];
       // re-base inherited tags to this block's first site
-      for (size_t j = 0; j < cy.size(); ++j) {
-        const ChainNode& src = nodes[cy[j].side == 0 ? nd.left : nd.right];
+      for (size_t j = 0; j < cys[b].size(); ++j) {
+        const ChainNode& src = nodes[cys[b][j].side == 0 ? nd.left : nd.right];
         blk->tags[j].site += src.lo - nd.lo;
       }
+      if (ids[b] != 0) cache[nd.sig] = blk;
+      blk_of[ids[b]] = blk;
     }
-    owned.push_back(blk);
-    if (!top) cache[nd.sig] = blk;
-    *out = blk_of[id] = blk;
-    return RMC_OK;
-  };
-  rmc_block* topb = nullptr;
-  rmc_status st = build(0, true, &topb);
-  if (st != RMC_OK) {
-    std::string e = ctx->err;
-    cleanup();
-    ctx->err = e;
-    return st;
+    for (int id : dup) blk_of[id] = cache[nodes[id].sig];
   }
+  rmc_block* topb = blk_of[0];
+  rmc_status st = RMC_OK;
   const int qe = std::min(q, topb->k);
   std::vector<double> E(qe);
   st = rmc_lowest(ctx, topb, q, E.data(), nullptr, nullptr);

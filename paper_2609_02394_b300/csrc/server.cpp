@@ -182,6 +182,7 @@ rmc_status rmc_server_create(const rmc_config* cfg_in, int slots, rmc_server** o
   std::unique_ptr<rmc_server> s(new rmc_server);
   if (cfg_in) s->cfg = *cfg_in;
   s->cfg.stream = nullptr;
+  s->cfg.lanes = 1;  // the slots already run whole solves concurrently
   s->budget = s->cfg.mem_budget ? s->cfg.mem_budget : ((size_t)40 << 30);
   for (int i = 0; i < slots; ++i) {
     rmc_ctx* c = nullptr;

@@ -133,3 +133,13 @@ def test_leaf_limits_are_rejected(ctx):
     with pytest.raises(P.RmcError) as e:
         ctx.solve_chain(I.tfim(30, 1.0, 0.9, 15, 16, 4))   # leaves of 15 sites
     assert e.value.status == P.RMC_ERR_INVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_level_batches_equal_one_merge_at_a_time(precision):
+    """rmc_solve_chain runs the merges of each level on the context's lanes;
+    the energies equal those of one merge at a time (lanes = 1) bit for bit."""
+    torch_cuda()
+    c = I.xxz(32, [1.0] * 31, 1.0, 4, 32, 6, fields=list(np.random.default_rng(61).uniform(-2, 2, 32)))
+    with P.Context(precision=precision, lanes=1) as one, P.Context(precision=precision) as many:
+        np.testing.assert_array_equal(one.solve_chain(c), many.solve_chain(c))

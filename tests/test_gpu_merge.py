@@ -227,3 +227,62 @@ def test_iteration_cap_reports_noconv():
         assert e.value.status == P.RMC_ERR_NOCONV
         blk = c.couple(hA, hB, terms, 40, allow_noconv=True)   # best iterate still returned
         assert blk.info()[0] >= 1
+
+
+def _prepare(ctx, case):
+    chain, Ar, Br, keep, top = MERGES[case]
+    A = O.leaf_block(chain, *Ar, chain.k)
+    B = O.leaf_block(chain, *Br, chain.k)
+    ref, _ = O.merge_blocks(chain, A, B, keep, top)
+    hA, kA_keys = _import(ctx, A)
+    hB, kB_keys = _import(ctx, B)
+    terms = [(c, kA_keys.index(ka), kB_keys.index(kb)) for c, ka, kb in O.merge_terms(chain, *Ar, *Br)]
+    keys = O.boundary_ops(chain, Ar[0], Br[1]) if not top else []
+    carry = [(0, kA_keys.index(k)) if k[0] < Ar[1] else (1, kB_keys.index(k)) for k in keys]
+    return (hA, hB, terms, keep, carry, top), ref, keys
+
+
+def test_batched_merges_match_one_at_a_time_and_the_oracle(ctx):
+    """rmc_couple_batch runs the independent merges at once (one stream and
+    host thread per lane, up to 8): every result equals the same merge run
+    alone (the kernels are deterministic) and the oracle's."""
+    cases = list(range(len(MERGES))) * 2
+    prep = [_prepare(ctx, c) for c in cases]
+    blocks = ctx.couple_batch([p[0] for p in prep])
+    etol, stol = TOL[ctx.precision]
+    for (args, ref, keys), blk in zip(prep, blocks):
+        E, ops, basis = blk.export()
+        alone = ctx.couple(*args[:5], top=args[5])
+        E1, ops1, basis1 = alone.export()
+        np.testing.assert_array_equal(E, E1)
+        np.testing.assert_array_equal(basis, basis1)
+        np.testing.assert_allclose(E, ref.E, atol=etol * max(1, np.abs(ref.E).max()))
+        assert overlap_singular_values(ref.U, basis.T).min() >= 1 - stol
+        for h in (blk, alone, args[0], args[1]):
+            h.free()
+
+
+def test_batch_reports_a_failing_merge_and_keeps_the_others(ctx):
+    prep = [_prepare(ctx, c) for c in (0, 2, 3)]
+    merges = [p[0] for p in prep]
+    bad = list(merges[1])
+    bad[2] = [(1.0, 99, 0)]                          # a term naming a missing operator
+    merges[1] = tuple(bad)
+    with pytest.raises(P.RmcError) as e:
+        ctx.couple_batch(merges)
+    assert e.value.status == P.RMC_ERR_INVAL
+    assert "missing operator" in ctx.last_error()
+
+
+def test_batch_lanes_share_the_budget():
+    """Lanes draw on their context's budget: a budget that holds the inputs
+    but not the merges' workspaces fails with NOMEM, and every byte the lanes
+    drew is returned to the context."""
+    torch_cuda()
+    with P.Context(precision="mixed", mem_budget=4 << 20) as c:
+        prep = [_prepare(c, 3) for _ in range(4)]
+        base = c.mem_in_use()
+        with pytest.raises(P.RmcError) as e:
+            c.couple_batch([p[0] for p in prep])
+        assert e.value.status == P.RMC_ERR_NOMEM
+        assert c.mem_in_use() == base
