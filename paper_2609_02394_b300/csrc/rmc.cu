@@ -65,6 +65,7 @@ struct rmc_ctx {
   rmc_ctx* acct = nullptr;  // context whose budget this one draws on (null: itself)
   std::mutex acct_mu;       // guards in_use of an accounting context
   std::vector<rmc_ctx*> lanes;
+  bool native64 = false;  // set while a kernel-level entry point runs (Native64Scope)
   rmc_config cfg{};
   std::string err;
   uint64_t launches = 0, iterations = 0;
@@ -240,7 +241,16 @@ void gemm_df(const double* A, const double* B, const GemmShape& s, int batches, 
 // The mixed paths form their FP64-accurate block products (Gram matrices and
 // basis combinations of the refinement and the rotations) in double-float;
 // the FP64 path keeps native FP64.
-inline bool fp64_by_df(const rmc_ctx* ctx) { return ctx->cfg.precision != RMC_PREC_FP64; }
+inline bool fp64_by_df(const rmc_ctx* ctx) { return ctx->cfg.precision != RMC_PREC_FP64 && !ctx->native64; }
+
+// Kernel-level entry points promise native FP64 for FP64 data whatever the
+// context's precision: this guard holds that for the duration of a call.
+struct Native64Scope {
+  rmc_ctx* ctx;
+  bool prev;
+  explicit Native64Scope(rmc_ctx* c) : ctx(c), prev(c->native64) { c->native64 = true; }
+  ~Native64Scope() { ctx->native64 = prev; }
+};
 
 // G (nv1 x nv2) = X1 X2^T, contraction over n, deterministic split-K.
 template <typename T>
@@ -326,16 +336,28 @@ rmc_status kron_apply(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y
   // contractions plus 3 kA kB for the diagonal term and the scaling
   ProfScope ps(ctx, sizeof(T) == 8 ? 1 : 0,
                (double)nv * ((double)2 * no * kA * kB * (kA + kB) + 3.0 * kA * kB));
+  bool df = false;  // the mixed paths form FP64-accurate products in double-FP32
+  if constexpr (sizeof(T) == 8) df = fp64_by_df(ctx);
   if (no > 0) {
     GemmShape s1{nv * kA, no * kB, kB, kB, kB, 0, 0, 1};
     EpiKron1<T> e1{Tbuf, kA, kB, nv};
-    gemm_big<T, false, true>(X, H.Bcat, s1, 1, e1, ctx->stream);
+    if constexpr (sizeof(T) == 8) {
+      if (df) gemm_df<false, true>(X, H.Bcat, s1, 1, e1, ctx->stream);
+      else gemm_big<T, false, true>(X, H.Bcat, s1, 1, e1, ctx->stream);
+    } else {
+      gemm_big<T, false, true>(X, H.Bcat, s1, 1, e1, ctx->stream);
+    }
     CKL();
   }
   GemmShape s2{kA, nv * kB, no * kA, (long)no * kA, (long)nv * kB, 0, 0, 1};
   EpiKron2<T> e2{X, Z, H.EA, H.EB, Y, kA, kB, alpha, beta, gamma};
   if (no > 0) {
-    gemm_big<T, false, false>(H.Acat, Tbuf, s2, 1, e2, ctx->stream);
+    if constexpr (sizeof(T) == 8) {
+      if (df) gemm_df<false, false>(H.Acat, Tbuf, s2, 1, e2, ctx->stream);
+      else gemm_big<T, false, false>(H.Acat, Tbuf, s2, 1, e2, ctx->stream);
+    } else {
+      gemm_big<T, false, false>(H.Acat, Tbuf, s2, 1, e2, ctx->stream);
+    }
   } else {
     // no coupling: K = 0, the GEMM loop is empty and only the epilogue runs
     GemmShape s0{kA, nv * kB, 0, 1, (long)nv * kB, 0, 0, 1};
@@ -1832,6 +1854,7 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
     return fail(ctx, RMC_ERR_INVAL, "rmc_kron_matvec: bad arguments");
   if (dtype == 2 && !tc_fits(kA, kB, n_ops))
     return fail(ctx, RMC_ERR_INVAL, "rmc_kron_matvec: shape outside the tensor-core kernel (n_ops*kB, kA <= 256)");
+  Native64Scope native(ctx);
   Workspace ws(ctx);
   Coefs cf{};
   for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
@@ -1871,6 +1894,7 @@ rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
       (fused != 0 && fused != 1) || (dtype == 3 && !fused))
     return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: bad arguments");
   if (deg > 0 && !(theta0 < a && a < ub)) return fail(ctx, RMC_ERR_INVAL, "rmc_cheb_filter: need theta0 < a < ub");
+  Native64Scope native(ctx);
   Workspace ws(ctx);
   Coefs cf{};
   for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
@@ -1953,6 +1977,7 @@ rmc_status rmc_rotate_op(rmc_ctx* ctx, int side, int kA, int kB, int kr, const d
   TRY(check_ctx(ctx));
   if ((side != 0 && side != 1) || kA < 1 || kB < 1 || kr < 1 || !C || !o || !out)
     return fail(ctx, RMC_ERR_INVAL, "rmc_rotate_op: bad arguments");
+  Native64Scope native(ctx);
   Workspace ws(ctx);
   const long n = (long)kA * kB;
   double* Tr;
