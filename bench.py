@@ -63,6 +63,7 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the tile-tuning solve before warm-up")
     ap.add_argument("--workload", default="xxz", choices=["xxz", "serving"],
                     help="xxz: the batched XXZ N=32 k=64 benchmark (default); serving: Poisson request "
                          "stream of mixed chains through the continuous-batching server")
@@ -342,6 +343,15 @@ def run_ours(args):
     seeds = batch_seeds(rank, args.batch, gold.keys())
     chains = [I.xxz_n32(s) for s in seeds]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # tile autotuning: one untimed solve of the first instance fills the
+    # process-wide table the server's slots then read
+    tiles = "untuned (first candidate of every product)"
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        with P.Context(device=local, precision=args.precision) as tctx:
+            tctx.autotune(chains[0])
+        tiles = (f"autotuned: {len(P.tune_dump().splitlines())} shape bins, one tuning solve "
+                 f"({time.perf_counter() - t0:.1f} s) before warm-up")
     srv = P.Server(slots=args.slots, device=local, precision=args.precision)
 
     def step():
@@ -435,6 +445,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "N": 32, "k": 64, "q": 8, "L0": 4, "delta": 1.0,
                        "batch_per_gpu": args.batch, "slots": args.slots, "precision": args.precision,
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)",
+                       "tiles": tiles,
                        "timing": "CUDA events after device-wide synchronisation (work spans the slots' streams)"},
             "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean(lat_ms),
                            "queue_p50": sorted(queue_ms)[len(queue_ms) // 2]},

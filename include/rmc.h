@@ -268,6 +268,93 @@ rmc_status rmc_solve_chain_states(rmc_ctx* ctx, const struct rmc_chain* chain, i
                                   const rmc_op_tag* obs, double* E_out, double* obs_out,
                                   double* psi_out);
 
+/* ---- per-merge truncation diagnostics (Sec. IV and Appendix B) ----------- */
+
+/* For a merge of modules A and B, P projects the merged block's Hilbert space
+ * onto the retained product sector span{|a>|b>} of A's and B's kept states and
+ * Q = I - P.  With H the merged block's Hamiltonian and V its inter-module
+ * coupling, the paper bounds the merge's ground-energy error by
+ *     0 <= a - E0 <= r(b, gamma) = (sqrt(gamma^2 + 4 b^2) - gamma) / 2 <= b^2 / gamma
+ * (Sec. IV, Appendix B), where a = lambda_min(PHP), b = ||PHQ||_2 = ||PVQ||_2,
+ * gamma = lambda_min(QHQ on range Q) - a, E0 = lambda_min(H). */
+typedef struct rmc_merge_diag {
+  int lo, mid, hi;   /* module A = sites [lo, mid), module B = [mid, hi) (chain-global)  */
+  int kA, kB, k;     /* kept states of A, of B, and of the merged block                   */
+  double a;          /* lowest eigenvalue of the merge's H_eff (Eq. (7)): the block's E[0] */
+  double b;          /* ||P V Q||_2 in Kronecker form (Appendix B's expression); NaN when V's
+                        operator products are not carried (b needs [O^s O^t] for every pair
+                        of coupling operators on one side: single-site Paulis multiply to
+                        carried Paulis, operators on two different sites of one module do
+                        not).  Equals ||P H Q||_2 when both modules' kept states are exact
+                        eigenstates of their own Hamiltonians (leaves); for merged modules
+                        H_A (x) I also leaks out of the sector and bH below is the bound's b */
+  double bH;         /* ||P H Q||_2 on the block's full space; NaN when not evaluated      */
+  double gamma;      /* lambda_min(QHQ) - a; +inf when Q = 0 (every state kept); NaN when
+                        the block is not evaluated on its full space                       */
+  double r;          /* r(bH, gamma) above; 0 when bH = 0 or Q = 0; NaN when not evaluated */
+  double E0;         /* exact ground energy of the merged block's own Hamiltonian; NaN when
+                        not evaluated                                                      */
+} rmc_merge_diag;
+
+/* b = ||P V Q||_2 for the merge of A and B with coupling V = sum_t coef_t
+ * o_A[op_a] (x) o_B[op_b] (the terms of rmc_couple), computed in Kronecker form
+ * on the device from b^2 = lambda_max(P V^2 P - (P V P)^2) on range(P)
+ * (Appendix B): P V P is the coupling of Eq. (7), and P V^2 P is assembled from
+ * the blocks' carried operators, since two Paulis on one site multiply to +-(a
+ * Pauli or the identity).  Blocks must be tagged with single-site Paulis and
+ * must carry every such product (the chain solver's blocks do for
+ * nearest-neighbour couplings); otherwise RMC_ERR_INVAL.  FP64 subspace
+ * iteration on the Kronecker sum -M, residual 1e-12.  *b_out on the host.
+ * Synchronises. */
+rmc_status rmc_merge_bound(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B, const rmc_term* terms,
+                           int n_terms, double* b_out);
+
+/* The chain solve of rmc_solve_chain_states (E_out[q] as there) plus one
+ * rmc_merge_diag per merge of the recursion tree, children before parents
+ * (post-order; merges of equal signature share their numbers).  *n_merges
+ * receives the number of merges; the first min(*n_merges, max_merges) records
+ * are written to diag.  a and b are evaluated for every merge; E0, bH, gamma
+ * and r for merged blocks of at most full_space_sites sites (<= 22, else
+ * RMC_ERR_INVAL; 0: none), on the block's 2^L computational basis by an FP64
+ * Krylov-Rayleigh-Ritz method with full reorthogonalisation (residual 1e-9
+ * relative, or the value settled to 1e-13): the lowest eigenvalue of the
+ * block's Hamiltonian, that of Q H Q on range(Q) with Q formed from the
+ * children's lifted kept states, and the largest of W^T H Q H W on the
+ * retained sector (W = U_A (x) U_B).  The paper evaluates these for its 10- and
+ * 20-site validation (Appendix B figure).
+ * Synchronises. */
+rmc_status rmc_solve_chain_bounds(rmc_ctx* ctx, const struct rmc_chain* chain, int full_space_sites,
+                                  int max_merges, rmc_merge_diag* diag, int* n_merges, double* E_out);
+
+/* ---- autotuned tile shapes --------------------------------------------- */
+
+/* The solver's block products (Gram matrices X1 X2^T over the product-basis
+ * vectors and basis combinations op(W) X, in FP32, FP64 or double-FP32) each
+ * have a short list of launch configurations (SIMT tiles of 64 x 64, 48 x 48
+ * or 32 x 32; for Gram matrices also the split-K factor).  A process-wide
+ * table maps a product's shape bin to its configuration; bins without an entry
+ * use the first (untuned) one.  rmc_autotune solves `chain` once with tuning
+ * on: every product whose bin is new times each candidate on its own operands
+ * (CUDA events on the context's stream; merges run one at a time) and records
+ * the fastest.  Candidates differ only in summation order, so results change
+ * at rounding level, well inside the solver's tolerances.  Call it while no
+ * other solve runs in the process (tuning is process-wide while it runs).
+ * E_out[q] receives the solve's energies (may be NULL).  Synchronises. */
+rmc_status rmc_autotune(rmc_ctx* ctx, const struct rmc_chain* chain, double* E_out);
+
+/* The table as text, one "key=choice" line per shape bin, into buf (at most
+ * len bytes including the terminating NUL; buf may be NULL).  Returns the
+ * bytes the whole text needs, NUL included.  Needs no GPU. */
+size_t rmc_tune_dump(char* buf, size_t len);
+
+/* Merge "key=choice" lines (as written by rmc_tune_dump) into the table.
+ * Returns the number of entries read, or -1 on a malformed line (entries
+ * before it are kept).  Needs no GPU. */
+int rmc_tune_load(const char* text);
+
+/* Empty the table (every product then uses its untuned configuration). */
+void rmc_tune_clear(void);
+
 typedef struct rmc_server rmc_server;
 
 /* A solve server: `slots` solves run at once, each on its own host worker

@@ -30,7 +30,8 @@ EXPORTED = [
     "rmc_kron_matvec_noalloc", "rmc_server_create", "rmc_server_destroy", "rmc_submit", "rmc_poll",
     "rmc_server_stats", "rmc_estimate_bytes", "rmc_solve_chains", "rmc_server_profile",
     "rmc_server_profile_read", "rmc_server_last_error", "rmc_cheb_filter", "rmc_solve_chain_states",
-    "rmc_couple_batch",
+    "rmc_couple_batch", "rmc_merge_bound", "rmc_solve_chain_bounds", "rmc_autotune", "rmc_tune_dump",
+    "rmc_tune_load", "rmc_tune_clear",
 ]
 PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
 
@@ -63,6 +64,12 @@ class rmc_couple_desc(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("terms", ctypes.POINTER(rmc_term)),
                 ("n_terms", ctypes.c_int), ("k_keep", ctypes.c_int), ("carry", ctypes.POINTER(rmc_carry)),
                 ("n_carry", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class rmc_merge_diag(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int), ("mid", ctypes.c_int), ("hi", ctypes.c_int), ("kA", ctypes.c_int),
+                ("kB", ctypes.c_int), ("k", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("bH", ctypes.c_double), ("gamma", ctypes.c_double), ("r", ctypes.c_double), ("E0", ctypes.c_double)]
 
 
 class rmc_chain(ctypes.Structure):
@@ -140,6 +147,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_cheb_filter": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, ip, dp, dp, dp, ip, vp], ip),
         "rmc_solve_chain_states": ([vp, P(rmc_chain), ip, P(rmc_op_tag), P(dp), P(dp), P(dp)], ip),
         "rmc_couple_batch": ([vp, ip, P(rmc_couple_desc), P(vp), P(ip)], ip),
+        "rmc_merge_bound": ([vp, vp, vp, P(rmc_term), ip, P(dp)], ip),
+        "rmc_autotune": ([vp, P(rmc_chain), P(dp)], ip),
+        "rmc_tune_dump": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_size_t),
+        "rmc_tune_load": ([cp], ip),
+        "rmc_tune_clear": ([], None),
+        "rmc_solve_chain_bounds": ([vp, P(rmc_chain), ip, ip, P(rmc_merge_diag), P(ip), P(dp)], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -162,6 +175,27 @@ def kron_matvec_noalloc(stream: int, dtype: int, kA: int, kB: int, n_ops: int, n
     return lib.rmc_kron_matvec_noalloc(stream or None, dtype, kA, kB, n_ops, nv, EA, EB, A or None, B or None,
                                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), X, Y, Z or None,
                                        alpha, beta, gamma)
+
+
+def tune_dump() -> str:
+    """The autotuner's table as text ("key=choice" lines)."""
+    lib = load_library()
+    n = lib.rmc_tune_dump(None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib.rmc_tune_dump(buf, n)
+    return buf.value.decode()
+
+
+def tune_load(text: str) -> int:
+    """Merge a table written by ``tune_dump``; returns the entries read."""
+    n = load_library().rmc_tune_load(text.encode())
+    if n < 0:
+        raise ValueError("malformed tuning table")
+    return n
+
+
+def tune_clear() -> None:
+    load_library().rmc_tune_clear()
 
 
 def _dptr(a: np.ndarray):
@@ -384,6 +418,41 @@ class Context:
         del keep
         self._check(st)
         return E, O[:n_obs], psi
+
+    def autotune(self, chain) -> np.ndarray:
+        """Solve ``chain`` once with tile autotuning on (fills the process-wide
+        table for its product shapes); returns its energies."""
+        c, keep = make_chain(chain)
+        E = np.full(chain.q, np.nan)
+        st = self.lib.rmc_autotune(self.h, ctypes.byref(c), _dptr(E))
+        del keep
+        self._check(st)
+        return E
+
+    def merge_bound(self, A: Block, B: Block, terms) -> float:
+        """b = ||P V Q||_2 of the merge of A and B with the coupling ``terms``
+        [(coef, op_a, op_b), ...] as for ``couple`` (Appendix B)."""
+        tt = (rmc_term * max(1, len(terms)))(*[rmc_term(c, a, b) for c, a, b in terms])
+        b = ctypes.c_double()
+        self._check(self.lib.rmc_merge_bound(self.h, A.handle, B.handle, tt, len(terms), ctypes.byref(b)))
+        return b.value
+
+    def solve_chain_bounds(self, chain, full_space_sites: int = 0):
+        """The chain solve plus the truncation diagnostics of every merge
+        (children before parents): returns (E[q], [dict(lo, mid, hi, kA, kB,
+        k, a, b, gamma, r, E0), ...]); gamma, r and E0 are evaluated for merged
+        blocks of at most ``full_space_sites`` sites (NaN otherwise)."""
+        c, keep = make_chain(chain)
+        E = np.full(chain.q, np.nan)
+        cap = max(1, 2 * chain.n_sites)
+        diag = (rmc_merge_diag * cap)()
+        n = ctypes.c_int()
+        st = self.lib.rmc_solve_chain_bounds(self.h, ctypes.byref(c), full_space_sites, cap, diag, ctypes.byref(n),
+                                             _dptr(E))
+        del keep
+        self._check(st)
+        out = [{f: getattr(diag[i], f) for f, _ in rmc_merge_diag._fields_} for i in range(min(n.value, cap))]
+        return E, out
 
     # ---- kernel-level entry points (device pointers) -------------------------
     def kron_matvec(self, dtype: int, kA: int, kB: int, n_ops: int, nv: int, EA: int, EB: int, A: int, B: int,

@@ -35,6 +35,7 @@
 #include "cheb_fused.cuh"
 #include "kernels.cuh"
 #include "umma.cuh"
+#include "bounds.cuh"
 
 using namespace rmc;
 
@@ -252,57 +253,163 @@ struct Native64Scope {
   ~Native64Scope() { ctx->native64 = prev; }
 };
 
+// ---------------------------------------------------------------------------
+// Autotuned tile shapes.  The block products of the solver (Gram matrices
+// X1 X2^T over long vectors, basis combinations op(W) X) come in a handful of
+// shapes per workload (b x b outputs with b = k_ret + guard, vectors of
+// k_A k_B), and the best tile and split-K factor depend on them: a 64 x 64
+// tile wastes 78 % of its work on a 96 x 96 Gram matrix's ragged edge, a
+// 48 x 48 tile none.  Every tunable product has a short list of candidate
+// launch configurations; outside tuning the table's choice for the product's
+// shape bin is used (the first candidate, the untuned default, when the bin
+// has no entry).  rmc_autotune runs a solve with tuning on: each product whose
+// bin has no entry yet times every candidate on its own operands (CUDA events
+// on the context's stream, one warm-up and three timed runs each, a
+// synchronisation per candidate) and stores the fastest.  All candidates
+// compute the same product; they differ in summation order only (rounding).
+// The table is process-wide (every context and server slot reads it) and can
+// be saved and restored as text (rmc_tune_dump / rmc_tune_load).
+// ---------------------------------------------------------------------------
+struct TuneTable {
+  std::mutex mu;
+  std::map<std::string, int> choice;
+  std::atomic<int> tuning{0};  // > 0 while rmc_autotune runs
+};
+TuneTable& tune_table() {
+  static TuneTable t;
+  return t;
+}
+
+// Shape bin of a dimension: exact up to 64, then multiples of 16 up to 512,
+// then the power of two above (keys stay few for the ragged k_eff of the cut).
+std::string tune_bin(long d) {
+  long b = d;
+  if (d > 64 && d <= 512) b = (d + 15) / 16 * 16;
+  else if (d > 512) { b = 1; while (b < d) b <<= 1; }
+  return std::to_string(b);
+}
+
+// Runs candidate `c` (0 <= c < ncand) of a product through `run(c)`; picks c
+// from the table, or by timing when tuning is on and the bin is new.
+template <class Run>
+rmc_status tuned_launch(rmc_ctx* ctx, const std::string& key, int ncand, Run&& run, bool may_time = true) {
+  TuneTable& tt = tune_table();
+  int c = -1;
+  {
+    std::lock_guard<std::mutex> lk(tt.mu);
+    auto it = tt.choice.find(key);
+    if (it != tt.choice.end() && it->second >= 0 && it->second < ncand) c = it->second;
+  }
+  if (c < 0 && may_time && tt.tuning.load() > 0 && ncand > 1) {
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    float best = INFINITY;
+    int arg = 0;
+    for (int i = 0; i < ncand; ++i) {
+      TRY(run(i));  // warm-up (and a first launch of the configuration)
+      CK(cudaEventRecord(e0, ctx->stream));
+      for (int r = 0; r < 3; ++r) TRY(run(i));
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; arg = i; }
+    }
+    ctx->event_pool.push_back(e0);
+    ctx->event_pool.push_back(e1);
+    std::lock_guard<std::mutex> lk(tt.mu);
+    tt.choice[key] = arg;
+    c = arg;
+  }
+  return run(c < 0 ? 0 : c);
+}
+
+// Tile presets of the SIMT GEMM, 256 threads each: 64 x 64 (4 x 4 a thread),
+// 48 x 48 (3 x 3), 32 x 32 (2 x 2); K steps of 16 (FP32) or 8 (FP64 and
+// double-float).
+template <typename T, bool TA, bool TB, class Epi, bool DF>
+void gemm_tile(int tile, const T* A, const T* B, const GemmShape& s, int batches, const Epi& epi, cudaStream_t st) {
+  constexpr int BK = sizeof(T) == 4 ? 16 : 8;
+  if (tile == 1) launch_gemm<T, 48, 48, BK, 3, 3, TA, TB, Epi, DF>(A, B, s, batches, epi, st);
+  else if (tile == 2) launch_gemm<T, 32, 32, BK, 2, 2, TA, TB, Epi, DF>(A, B, s, batches, epi, st);
+  else launch_gemm<T, 64, 64, BK, 4, 4, TA, TB, Epi, DF>(A, B, s, batches, epi, st);
+}
+
 // G (nv1 x nv2) = X1 X2^T, contraction over n, deterministic split-K.
+// Candidates: tile in {64, 48, 32} x split-K in {s, s/2, 2s}, s the default
+// split count (about two CTA waves of the 64 x 64 tiling, >= 128 terms a split).
 template <typename T>
 rmc_status gram(rmc_ctx* ctx, Workspace& ws, const T* X1, int nv1, const T* X2, int nv2, long n, T* G,
                 bool symmetrize) {
   ProfScope ps(ctx, 4, 2.0 * nv1 * nv2 * (double)n);
-  const int tiles = (int)(ceil_div(nv1, 64) * ceil_div(nv2, 64));
-  int splits = (int)std::min<long>(std::max<long>(1, n / 128), std::max(1, 296 / tiles));
-  splits = std::min(splits, 64);
+  bool df = false;
+  if constexpr (sizeof(T) == 8) df = fp64_by_df(ctx);
+  const int tiles64 = (int)(ceil_div(nv1, 64) * ceil_div(nv2, 64));
+  const int base = std::min(64, (int)std::min<long>(std::max<long>(1, n / 128), std::max(1, 296 / tiles64)));
+  const int max_split = (int)std::min<long>(std::max<long>(1, n / 64), 128);
+  auto splits_of = [&](int c) {
+    const int m = c % 3;
+    const int sp = m == 0 ? base : m == 1 ? std::max(1, base / 2) : 2 * base;
+    return std::max(1, std::min(sp, max_split));
+  };
   T* P = nullptr;
-  TRY(ws.get(&P, (size_t)splits * nv1 * nv2));
-  GemmShape s{nv1, nv2, (int)n, n, n, 0, 0, splits};
-  EpiStore<T> epi{P, nv2, 0, (long)nv1 * nv2, T(1), T(0)};
-  if constexpr (sizeof(T) == 8) {
-    if (fp64_by_df(ctx)) {
-      gemm_df<false, true>(X1, X2, s, 1, epi, ctx->stream);
-      CKL();
-      reduce_splits_kernel<T><<<grid1d((long)nv1 * nv2), 256, 0, ctx->stream>>>(
-          P, splits, (long)nv1 * nv2, nv1, nv2, G, nv2, T(1), T(0), symmetrize ? 1 : 0);
-      CKL();
-      return RMC_OK;
+  TRY(ws.get(&P, (size_t)std::max(base, std::min(2 * base, max_split)) * nv1 * nv2));
+  // the untuned default keeps the historical choice: 16 x 16 tiles for small
+  // native outputs, else 64 x 64, with the base split
+  const bool small = !df && nv1 <= 32 && nv2 <= 32;
+  auto run = [&](int c) -> rmc_status {
+    const int sp = splits_of(c);
+    GemmShape s{nv1, nv2, (int)n, n, n, 0, 0, sp};
+    EpiStore<T> epi{P, nv2, 0, (long)nv1 * nv2, T(1), T(0)};
+    const int tile = c / 3;
+    if constexpr (sizeof(T) == 8) {
+      if (df) gemm_tile<T, false, true, EpiStore<T>, true>(tile, X1, X2, s, 1, epi, ctx->stream);
+      else if (small && c == 0) gemm_small<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
+      else gemm_tile<T, false, true, EpiStore<T>, false>(tile, X1, X2, s, 1, epi, ctx->stream);
+    } else {
+      if (small && c == 0) gemm_small<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
+      else gemm_tile<T, false, true, EpiStore<T>, false>(tile, X1, X2, s, 1, epi, ctx->stream);
     }
-  }
-  if (nv1 <= 32 && nv2 <= 32) gemm_small<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
-  else gemm_big<T, false, true>(X1, X2, s, 1, epi, ctx->stream);
-  CKL();
-  reduce_splits_kernel<T><<<grid1d((long)nv1 * nv2), 256, 0, ctx->stream>>>(P, splits, (long)nv1 * nv2, nv1, nv2, G,
-                                                                             nv2, T(1), T(0), symmetrize ? 1 : 0);
-  CKL();
-  return RMC_OK;
+    CKL();
+    reduce_splits_kernel<T><<<grid1d((long)nv1 * nv2), 256, 0, ctx->stream>>>(
+        P, sp, (long)nv1 * nv2, nv1, nv2, G, nv2, T(1), T(0), symmetrize ? 1 : 0);
+    CKL();
+    return RMC_OK;
+  };
+  const std::string key = std::string("gram|") + (df ? "df" : sizeof(T) == 8 ? "f64" : "f32") + "|" +
+                          tune_bin(nv1) + "x" + tune_bin(nv2) + "|" + tune_bin(n);
+  return tuned_launch(ctx, key, 9, run);
 }
 
 // Out (nvo x n) = alpha * op(W) X + beta * Src; op(W) = W (nvo x nvi) or W^T
-// (W stored nvi x nvo).
+// (W stored nvi x nvo).  Candidates: tile in {64, 48, 32}; tuning is skipped
+// (default tile) when Out aliases an input, since every timed run must leave
+// the same result.
 template <typename T>
 rmc_status combine(rmc_ctx* ctx, const T* W, bool transW, int nvo, int nvi, const T* X, long n, T* Out, T alpha,
                    T beta, const T* Src) {
   ProfScope ps(ctx, 5, 2.0 * nvo * nvi * (double)n);
   GemmShape s{nvo, (int)n, nvi, transW ? nvo : nvi, n, 0, 0, 1};
   EpiAxpby<T> epi{Out, Src, n, n, 0, 0, alpha, beta};
-  if constexpr (sizeof(T) == 8) {
-    if (fp64_by_df(ctx)) {
-      if (transW) gemm_df<true, false>(W, X, s, 1, epi, ctx->stream);
-      else gemm_df<false, false>(W, X, s, 1, epi, ctx->stream);
-      CKL();
-      return RMC_OK;
+  bool df = false;
+  if constexpr (sizeof(T) == 8) df = fp64_by_df(ctx);
+  auto run = [&](int tile) -> rmc_status {
+    if constexpr (sizeof(T) == 8) {
+      if (df) {
+        if (transW) gemm_tile<T, true, false, EpiAxpby<T>, true>(tile, W, X, s, 1, epi, ctx->stream);
+        else gemm_tile<T, false, false, EpiAxpby<T>, true>(tile, W, X, s, 1, epi, ctx->stream);
+        CKL();
+        return RMC_OK;
+      }
     }
-  }
-  if (transW) gemm_big<T, true, false>(W, X, s, 1, epi, ctx->stream);
-  else gemm_big<T, false, false>(W, X, s, 1, epi, ctx->stream);
-  CKL();
-  return RMC_OK;
+    if (transW) gemm_tile<T, true, false, EpiAxpby<T>, false>(tile, W, X, s, 1, epi, ctx->stream);
+    else gemm_tile<T, false, false, EpiAxpby<T>, false>(tile, W, X, s, 1, epi, ctx->stream);
+    CKL();
+    return RMC_OK;
+  };
+  const bool aliased = Out == X || Out == W || (beta != T(0) && Out == Src);
+  const std::string key = std::string("comb|") + (df ? "df" : sizeof(T) == 8 ? "f64" : "f32") +
+                          (transW ? "|t|" : "|n|") + tune_bin(nvo) + "x" + tune_bin(nvi) + "|" + tune_bin(n);
+  return tuned_launch(ctx, key, 3, run, !aliased);
 }
 
 // C (m x m) = alpha op(A) op(B) + beta Src for the small Rayleigh-Ritz products.
@@ -894,7 +1001,8 @@ inline double worst_relative(const std::vector<double>& r, const std::vector<dou
 
 template <typename W>
 rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_conv, const int* d_idx,
-                 double ub, double tol, int max_iter, W* X, W* HX, W* theta, int* iters_out, bool* converged) {
+                 double ub, double tol, int max_iter, W* X, W* HX, W* theta, int* iters_out, bool* converged,
+                 bool value_only = false) {
   const long n = H.n();
   W *Y0, *Y1, *Y2, *Tbuf, *G, *Z, *tmp;
   double* rn;
@@ -936,12 +1044,22 @@ rmc_status chfsi(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b, int k_c
   TRY(rayleigh_ritz());
   std::vector<double> th(b), r(b);
   StallGuard stall;
-  int it = 0;
+  int it = 0, steady = 0;
+  double th0_prev = NAN;
   *converged = false;
   for (;; ++it) {
     int fails = 0;
     TRY(read_status(ctx, &fails, 1));
     TRY(to_host<W>(ctx, theta, th.data(), b));
+    // value_only: the caller needs the lowest Ritz value alone, which
+    // converges quadratically in the residual; inside a tight cluster the
+    // Ritz vectors (and their residuals) settle much later than the value,
+    // so a value unchanged to 1e-13 over three iterations counts as converged
+    if (value_only) {
+      steady = std::fabs(th[0] - th0_prev) <= 1e-13 * std::max(1.0, std::fabs(th[0])) ? steady + 1 : 0;
+      th0_prev = th[0];
+      if (steady >= 3) fails = 0;
+    }
     double worst = 0;
     int wi = 0;
     if (ctx->trace || (!fp64 && fails > 0)) {
@@ -2029,6 +2147,11 @@ constexpr int kDenseLeafSites = 7;
 // 2^N computational basis (2^24 doubles = 128 MiB per state).
 constexpr int kMaxLiftSites = 24;
 
+// Largest merged block whose exact ground energy and discarded-sector gap
+// rmc_solve_chain_bounds evaluates on the full 2^L basis (Krylov vectors of
+// 2^22 doubles, 32 MiB each, 96 of them and their products: 6 GiB).
+constexpr int kMaxFullSpaceSites = 22;
+
 int build_tree(std::vector<ChainNode>& nodes, int lo, int hi, int L0) {
   nodes.push_back(ChainNode{lo, hi});
   const int id = (int)nodes.size() - 1;
@@ -2105,13 +2228,339 @@ rmc_status lift_block(rmc_ctx* ctx, Workspace& ws, const std::vector<ChainNode>&
   return RMC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Per-merge truncation diagnostics (Sec. IV and Appendix B).  For the merge
+// of blocks A and B let P project the merged block's Hilbert space onto the
+// retained product sector span{|a>|b>} (the kept states of A and B) and
+// Q = I - P.  Then a = lambda_min(PHP) is the merge's lowest eigenvalue of
+// Eq. (7), b = ||PHQ||_2 = ||PVQ||_2 (the uncoupled part does not mix the
+// sectors), gamma = lambda_min(QHQ on range Q) - a, and the merge's error
+// obeys 0 <= a - E0 <= r(b, gamma) = (sqrt(gamma^2 + 4 b^2) - gamma) / 2.
+// ---------------------------------------------------------------------------
+
+// Product of two real single-site Paulis (Y carried as iY): p1 p2 = sign * out,
+// out = 'I' for the identity.  Returns false for a non-Pauli tag.
+bool pauli_product(char p1, char p2, char* out, double* sign) {
+  auto idx = [](char p) { return p == 'X' ? 0 : p == 'Y' ? 1 : p == 'Z' ? 2 : -1; };
+  const int i = idx(p1), j = idx(p2);
+  if (i < 0 || j < 0) return false;
+  // rows: p1 = X, iY, Z; columns: p2 = X, iY, Z (matrix products of the real forms)
+  static const char prod[3][3] = {{'I', 'Z', 'Y'}, {'Z', 'I', 'X'}, {'Y', 'X', 'I'}};
+  static const double sgn[3][3] = {{1, -1, -1}, {1, -1, -1}, {1, 1, 1}};
+  *out = prod[i][j];
+  *sign = sgn[i][j];
+  return true;
+}
+
+// b = ||P V Q||_2 of the merge of A and B with coupling V = sum_t c_t O_A^t (x) O_B^t,
+// from b^2 = lambda_max(P V^2 P - (P V P)^2) restricted to range(P) (Appendix B).
+// In the product basis of the kept states
+//   P V P   = sum_t c_t o_A^t (x) o_B^t                  (the coupling of Eq. (7)),
+//   P V^2 P = sum_{s,t} c_s c_t [O_A^s O_A^t] (x) [O_B^s O_B^t],
+// with [O] = U^T O U the projection of a physical operator onto a block's kept
+// states.  Two Paulis on one site multiply to +-(a Pauli or I), so [O^s O^t] is
+// a carried operator up to sign, or the identity; a product of operators on
+// different sites is not carried, and then b is unavailable (*available =
+// false, *b_out = NaN).  M = P V^2 P - (P V P)^2 is itself a Kronecker sum, so
+// lambda_max(M) = -lambda_min(-M) comes from the merge's own FP64 subspace
+// iteration on -M.
+rmc_status coupling_norm(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B, const rmc_term* terms, int nt,
+                         double* b_out, bool* available, std::string* why) {
+  *available = false;
+  *b_out = NAN;
+  const int kA = A->k, kB = B->k;
+  const long n = (long)kA * kB;
+  if (nt == 0) {
+    *available = true;
+    *b_out = 0.0;
+    return RMC_OK;
+  }
+  struct KTerm { int ia, ib; int qs, qt; double coef; };  // ia/ib: carried op, -1 identity; q: -1 or (s, t)
+  std::vector<KTerm> kt;
+  for (int s = 0; s < nt; ++s)
+    for (int t = 0; t < nt; ++t) {
+      const rmc_op_tag as = A->tags[terms[s].op_a], at = A->tags[terms[t].op_a];
+      const rmc_op_tag bs = B->tags[terms[s].op_b], bt = B->tags[terms[t].op_b];
+      char pa, pb;
+      double sa, sb;
+      if (as.site != at.site || bs.site != bt.site || !pauli_product(as.pauli, at.pauli, &pa, &sa) ||
+          !pauli_product(bs.pauli, bt.pauli, &pb, &sb)) {
+        *why = "the coupling's operator products are not single-site Paulis";
+        return RMC_OK;
+      }
+      const int ia = pa == 'I' ? -1 : find_tag(A, as.site, pa);
+      const int ib = pb == 'I' ? -1 : find_tag(B, bs.site, pb);
+      if ((pa != 'I' && ia < 0) || (pb != 'I' && ib < 0)) {
+        *why = "an operator product is not carried by the blocks";
+        return RMC_OK;
+      }
+      // -M = -P V^2 P + (P V P)^2: the product term enters negated
+      const double c = -terms[s].coef * terms[t].coef * sa * sb;
+      bool merged = false;
+      for (KTerm& k : kt)
+        if (k.qs < 0 && k.ia == ia && k.ib == ib) { k.coef += c; merged = true; break; }
+      if (!merged) kt.push_back(KTerm{ia, ib, -1, -1, c});
+    }
+  for (int s = 0; s < nt; ++s)
+    for (int t = 0; t < nt; ++t) kt.push_back(KTerm{-1, -1, s, t, terms[s].coef * terms[t].coef});
+  const int no = (int)kt.size();
+  if (no > kMaxOps) {
+    *why = "too many coupling terms for the product operator";
+    return RMC_OK;
+  }
+  Workspace ws(ctx);
+  double *Am, *Bm, *Acat, *EA, *EB, *D, *dmm;
+  int* idx;
+  TRY(ws.get(&Am, (size_t)no * kA * kA));
+  TRY(ws.get(&Bm, (size_t)no * kB * kB));
+  TRY(ws.get(&Acat, (size_t)no * kA * kA));
+  TRY(ws.get(&EA, kA));
+  TRY(ws.get(&EB, kB));
+  TRY(ws.get(&D, n));
+  TRY(ws.get(&dmm, 2));
+  CK(cudaMemsetAsync(EA, 0, sizeof(double) * kA, ctx->stream));
+  CK(cudaMemsetAsync(EB, 0, sizeof(double) * kB, ctx->stream));
+  Coefs cf{};
+  double norm_bound = 0.0;
+  auto put = [&](const rmc_block* X, int k, int i, double* dst) -> rmc_status {
+    if (i < 0) {
+      identity_fill_kernel<<<grid1d((long)k * k), 256, 0, ctx->stream>>>(dst, k);
+      CKL();
+    } else {
+      CK(cudaMemcpyAsync(dst, X->ops + (size_t)i * k * k, sizeof(double) * k * k, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+    }
+    return RMC_OK;
+  };
+  for (int j = 0; j < no; ++j) {
+    const KTerm& t = kt[j];
+    double* aj = Am + (size_t)j * kA * kA;
+    double* bj = Bm + (size_t)j * kB * kB;
+    cf.c[j] = t.coef;
+    if (t.qs < 0) {
+      TRY(put(A, kA, t.ia, aj));
+      TRY(put(B, kB, t.ib, bj));
+      norm_bound += std::fabs(t.coef) * (t.ia < 0 ? 1.0 : A->opnorm[t.ia]) * (t.ib < 0 ? 1.0 : B->opnorm[t.ib]);
+    } else {
+      // o^s o^t of the projected operators (the square of the coupling of Eq. (7))
+      const int as = terms[t.qs].op_a, at = terms[t.qt].op_a, bs = terms[t.qs].op_b, bt = terms[t.qt].op_b;
+      TRY((small_mm<double, false, false>(ctx, A->ops + (size_t)as * kA * kA, A->ops + (size_t)at * kA * kA, kA, aj,
+                                          1.0, 0.0, nullptr)));
+      TRY((small_mm<double, false, false>(ctx, B->ops + (size_t)bs * kB * kB, B->ops + (size_t)bt * kB * kB, kB, bj,
+                                          1.0, 0.0, nullptr)));
+      norm_bound += std::fabs(t.coef) * A->opnorm[as] * A->opnorm[at] * B->opnorm[bs] * B->opnorm[bt];
+    }
+  }
+  build_acat_kernel<double><<<grid1d((long)kA * kA * no), 256, 0, ctx->stream>>>(Am, cf, kA, no, Acat);
+  CKL();
+  KronOp<double> K;
+  K.kA = kA;
+  K.kB = kB;
+  K.n_ops = no;
+  K.EA = EA;
+  K.EB = EB;
+  K.Acat = Acat;
+  K.Bcat = Bm;
+  // start block: the smallest diagonal entries of -M; the whole space when it is small
+  const int bsz = (int)std::min<long>(n, n <= 48 ? n : 32);
+  TRY(ws.get(&idx, bsz));
+  diag_kernel<<<grid1d(n), 256, 0, ctx->stream>>>(EA, EB, Am, Bm, cf, no, kA, kB, D);
+  CKL();
+  select_smallest_kernel<<<1, 1024, 0, ctx->stream>>>(D, n, bsz, idx, dmm);
+  CKL();
+  double hdmm[2];
+  TRY(to_host<double>(ctx, dmm, hdmm, 2));
+  const double ub = hdmm[1] + norm_bound + 1e-12 * std::max(1.0, hdmm[1] + norm_bound);
+  double *X, *HX, *th;
+  TRY(ws.get(&X, (size_t)bsz * n));
+  TRY(ws.get(&HX, (size_t)bsz * n));
+  TRY(ws.get(&th, bsz));
+  int iters = 0;
+  bool conv = false;
+  TRY((chfsi<double>(ctx, ws, K, bsz, 1, idx, ub, 1e-11, ctx->cfg.max_iter, X, HX, th, &iters, &conv, true)));
+  double th0 = 0.0;
+  TRY(to_host<double>(ctx, th, &th0, 1));
+  if (!conv) return fail(ctx, RMC_ERR_NOCONV, "coupling norm: the eigensolve did not converge in %d iterations", iters);
+  *b_out = std::sqrt(std::max(0.0, -th0));
+  *available = true;
+  return RMC_OK;
+}
+
+// The merged block's Hamiltonian on its own 2^L computational basis and the
+// projector onto the retained product sector, P = W W^T with W = U_A (x) U_B
+// (U_A: kA lifted kept states of A, vector-major kA x 2^LA; U_B likewise).
+struct FullSpace {
+  int L = 0;
+  long dim = 0;
+  const FullTerm* terms = nullptr;  // device
+  int nt = 0;
+  const double* UA = nullptr;
+  const double* UB = nullptr;
+  int kA = 0, kB = 0, LA = 0, LB = 0;
+};
+
+// out = x - P x: c = U_A X U_B^T (X the 2^LA x 2^LB reshaping of x, A's sites
+// the more significant bits), then P x = U_A^T c U_B.
+rmc_status project_q(rmc_ctx* ctx, const FullSpace& fs, const double* x, double* out) {
+  Workspace ws(ctx);
+  const long nA = 1L << fs.LA, nB = 1L << fs.LB;
+  double *G1, *Cm, *T2;
+  TRY(ws.get(&G1, (size_t)nA * fs.kB));
+  TRY(ws.get(&Cm, (size_t)fs.kA * fs.kB));
+  TRY(ws.get(&T2, (size_t)fs.kA * nB));
+  TRY(gram<double>(ctx, ws, x, (int)nA, fs.UB, fs.kB, nB, G1, false));
+  TRY(combine<double>(ctx, fs.UA, false, fs.kA, (int)nA, G1, fs.kB, Cm, 1.0, 0.0, nullptr));
+  TRY(combine<double>(ctx, Cm, false, fs.kA, fs.kB, fs.UB, nB, T2, 1.0, 0.0, nullptr));
+  TRY(combine<double>(ctx, fs.UA, true, (int)nA, fs.kA, T2, nB, out, -1.0, 1.0, x));
+  return RMC_OK;
+}
+
+// Lowest eigenvalue of a symmetric operator S on R^n by a Krylov-Rayleigh-Ritz
+// method in FP64: Lanczos vectors with two classical Gram-Schmidt passes
+// against all earlier ones (full reorthogonalisation), the Rayleigh-Ritz
+// matrix V^T S V formed from the stored products, explicit restarts from the
+// lowest Ritz vector.  apply(x, y) sets y = S x; keep(x, tmp) maps x into the
+// invariant subspace the solve is restricted to (in place, tmp a scratch
+// vector; a no-op for the whole space).  Converged when the Ritz vector's
+// residual is below tol * max(1, |theta|), when the Krylov space is exhausted
+// (its Ritz values are then exact), or when theta has not moved by 1e-13
+// relative over 16 steps (the value alone is wanted, and a near-degenerate
+// partner can keep the vector's residual up long after the value settled).
+template <class Apply, class Keep>
+rmc_status krylov_lowest(rmc_ctx* ctx, long n, long dim_eff, double tol, Apply&& apply, Keep&& keep, double* lam) {
+  const int m = (int)std::min<long>(96, dim_eff);
+  constexpr int kRestarts = 30;
+  Workspace ws(ctx);
+  double *V, *SV, *tmp, *h, *G, *w, *Z, *z0, *x0, *sx0, *rn, *nrm;
+  TRY(ws.get(&V, (size_t)m * n));
+  TRY(ws.get(&SV, (size_t)m * n));
+  TRY(ws.get(&tmp, (size_t)n));
+  TRY(ws.get(&x0, (size_t)n));
+  TRY(ws.get(&sx0, (size_t)n));
+  TRY(ws.get(&h, (size_t)m));
+  TRY(ws.get(&G, (size_t)m * m));
+  TRY(ws.get(&w, (size_t)m));
+  TRY(ws.get(&Z, (size_t)m * m));
+  TRY(ws.get(&z0, (size_t)m * m));
+  TRY(ws.get(&rn, 1));
+  TRY(ws.get(&nrm, 1));
+  seeded_vector_kernel<<<grid1d(n), 256, 0, ctx->stream>>>(V, n, 2609ull);
+  CKL();
+  TRY(keep(V, tmp));
+  normalize_kernel<double><<<1, 1024, 0, ctx->stream>>>(V, n, nullptr);
+  CKL();
+  double th_prev = NAN;
+  for (int rs = 0; rs < kRestarts; ++rs) {
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      TRY(apply(vj, SV + (size_t)j * n));
+      bool breakdown = false;
+      if (j + 1 < m) {
+        double* vn = V + (size_t)(j + 1) * n;
+        CK(cudaMemcpyAsync(vn, SV + (size_t)j * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int pass = 0; pass < 2; ++pass) {
+          Workspace wl(ctx);
+          TRY(gram<double>(ctx, wl, V, j + 1, vn, 1, n, h, false));  // h = V vn (j+1 x 1)
+          TRY(combine<double>(ctx, h, true, 1, j + 1, V, n, tmp, -1.0, 1.0, vn));
+          CK(cudaMemcpyAsync(vn, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        TRY(keep(vn, tmp));
+        normalize_kernel<double><<<1, 1024, 0, ctx->stream>>>(vn, n, nrm);
+        CKL();
+        double hn = 0.0;
+        TRY(to_host<double>(ctx, nrm, &hn, 1));
+        breakdown = !(hn > 1e-10);  // the Krylov space is invariant: its Ritz values are exact
+      }
+      const int mj = j + 1;
+      if (!(mj % 16 == 0 || mj == m || breakdown)) continue;
+      Workspace wl(ctx);
+      TRY(gram<double>(ctx, wl, V, mj, SV, mj, n, G, true));
+      TRY(syev64(ctx, wl, G, mj, w, Z));
+      columns_to_vectors_kernel<double><<<grid1d((long)mj), 256, 0, ctx->stream>>>(Z, mj, 1, z0);
+      CKL();
+      TRY(combine<double>(ctx, z0, false, 1, mj, V, n, x0, 1.0, 0.0, nullptr));
+      TRY(combine<double>(ctx, z0, false, 1, mj, SV, n, sx0, 1.0, 0.0, nullptr));
+      CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+      residual_kernel<double><<<1, 1024, 0, ctx->stream>>>(x0, sx0, w, n, 1, tol, rn, ctx->d_status);
+      CKL();
+      int fails = 0;
+      TRY(read_status(ctx, &fails, 1));
+      double th0 = 0.0;
+      TRY(to_host<double>(ctx, w, &th0, 1));
+      const bool steady = std::fabs(th0 - th_prev) <= 1e-13 * std::max(1.0, std::fabs(th0));
+      th_prev = th0;
+      if (fails == 0 || breakdown || steady) {
+        *lam = th0;
+        return RMC_OK;
+      }
+      if (mj == m) break;
+    }
+    // restart from the lowest Ritz vector
+    CK(cudaMemcpyAsync(V, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    TRY(keep(V, tmp));
+    normalize_kernel<double><<<1, 1024, 0, ctx->stream>>>(V, n, nullptr);
+    CKL();
+  }
+  return fail(ctx, RMC_ERR_NOCONV, "Krylov eigensolve did not converge (dimension %ld)", n);
+}
+
+// out (2^L) = W x = U_A^T X U_B for x the kA x kB coefficient matrix X of a
+// product-basis vector of the merge (its state lifted to the block's basis).
+rmc_status lift_product(rmc_ctx* ctx, const FullSpace& fs, const double* x, double* out) {
+  Workspace ws(ctx);
+  const long nB = 1L << fs.LB;
+  double* T1;
+  TRY(ws.get(&T1, (size_t)fs.kA * nB));
+  TRY(combine<double>(ctx, x, false, fs.kA, fs.kB, fs.UB, nB, T1, 1.0, 0.0, nullptr));
+  TRY(combine<double>(ctx, fs.UA, true, (int)(1L << fs.LA), fs.kA, T1, nB, out, 1.0, 0.0, nullptr));
+  return RMC_OK;
+}
+
+// out (kA x kB) = alpha W^T y = alpha U_A Y U_B^T: a block-basis vector's
+// coefficients in the retained product basis.
+rmc_status restrict_product(rmc_ctx* ctx, const FullSpace& fs, const double* y, double* out, double alpha) {
+  Workspace ws(ctx);
+  const long nA = 1L << fs.LA, nB = 1L << fs.LB;
+  double* G1;
+  TRY(ws.get(&G1, (size_t)nA * fs.kB));
+  TRY(gram<double>(ctx, ws, y, (int)nA, fs.UB, fs.kB, nB, G1, false));
+  TRY(combine<double>(ctx, fs.UA, false, fs.kA, (int)nA, G1, fs.kB, out, alpha, 0.0, nullptr));
+  return RMC_OK;
+}
+
+// Pauli-string terms of the block [lo, hi) of a chain, on its own sites.
+std::vector<FullTerm> block_full_terms(const std::vector<CTerm>& terms, int lo, int hi) {
+  const int L = hi - lo;
+  std::vector<FullTerm> out;
+  auto bit = [&](int site) { return 1ull << (L - 1 - (site - lo)); };
+  auto add = [&](FullTerm& f, int site, char p) {
+    if (p == 'X' || p == 'Y') f.flip |= bit(site);
+    if (p == 'Z' || p == 'Y') f.sign |= bit(site);
+  };
+  for (const CTerm& t : terms) {
+    const bool in = t.j < 0 ? (t.i >= lo && t.i < hi) : (t.i >= lo && t.j < hi);
+    if (!in) continue;
+    FullTerm f{0, 0, t.coef};
+    add(f, t.i, t.pi);
+    if (t.j >= 0) {
+      add(f, t.j, t.pj);
+      if (t.pi == 'Y' && t.pj == 'Y') f.coef = -t.coef;  // YY = -(iY)(iY)
+    } else if (t.pi == 'Y') {
+      f.coef = NAN;  // a lone Y is imaginary: not a real Hamiltonian term
+    }
+    out.push_back(f);
+  }
+  return out;
+}
+
 // The recursion loop of Algorithm 1 over a chain, optionally carrying extra
 // single-site operators (observables) to the top and lifting the top states.
 rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int n_onsite, const int* onsite_site,
                             const char* onsite_pauli, const double* onsite_coef, int n_bonds, const int* bond_i,
                             const int* bond_j, const char* bond_pauli_i, const char* bond_pauli_j,
                             const double* bond_coef, int n_obs, const rmc_op_tag* obs, double* E_out,
-                            double* obs_out, double* psi_out) {
+                            double* obs_out, double* psi_out, int diag_sites = 0, int max_diag = 0,
+                            rmc_merge_diag* diag = nullptr, int* n_diag = nullptr) {
   TRY(check_ctx(ctx));
   if (n_sites < 1 || L0 < 1 || k < 1 || q < 1 || n_onsite < 0 || n_bonds < 0 || !E_out || n_obs < 0 ||
       (n_obs > 0 && (!obs || !obs_out)))
@@ -2240,6 +2689,22 @@ rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int
     if (!top) cache[nd.sig] = blk;
     blk_of[id] = blk;
   }
+  // coupling terms of the merge at an inner node, in its children's carried operators
+  auto merge_terms_of = [&](int id, std::vector<rmc_term>* mt) -> bool {
+    const ChainNode& nd = nodes[id];
+    const rmc_block* A = blk_of[nd.left];
+    const rmc_block* B = blk_of[nd.right];
+    const int Alo = nodes[nd.left].lo, Blo = nodes[nd.right].lo, Bhi = nodes[nd.right].hi;
+    mt->clear();
+    for (const CTerm& t : terms) {
+      if (t.j < 0 || !(t.i >= Alo && t.i < Blo && t.j >= Blo && t.j < Bhi)) continue;
+      const int oa = find_tag(A, t.i - Alo, t.pi), ob = find_tag(B, t.j - Blo, t.pj);
+      if (oa < 0 || ob < 0) return false;
+      // Y Y = -(iY)(iY): carried Y operators are iY
+      mt->push_back(rmc_term{(t.pi == 'Y' && t.pj == 'Y') ? -t.coef : t.coef, oa, ob});
+    }
+    return true;
+  };
   for (int h = 1; h <= height[0]; ++h) {
     std::vector<int> ids, dup;
     std::set<std::string> queued;
@@ -2258,15 +2723,10 @@ rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int
       }
       const rmc_block* A = blk_of[nd.left];
       const rmc_block* B = blk_of[nd.right];
-      const int Alo = nodes[nd.left].lo, Blo = nodes[nd.right].lo, Bhi = nodes[nd.right].hi;
+      const int Alo = nodes[nd.left].lo, Blo = nodes[nd.right].lo;
       std::vector<rmc_term> mt;
-      for (const CTerm& t : terms) {
-        if (t.j < 0 || !(t.i >= Alo && t.i < Blo && t.j >= Blo && t.j < Bhi)) continue;
-        const int oa = find_tag(A, t.i - Alo, t.pi), ob = find_tag(B, t.j - Blo, t.pj);
-        if (oa < 0 || ob < 0) return bail(fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing carried operator"));
-        // Y Y = -(iY)(iY): carried Y operators are iY
-        mt.push_back(rmc_term{(t.pi == 'Y' && t.pj == 'Y') ? -t.coef : t.coef, oa, ob});
-      }
+      if (!merge_terms_of((int)id, &mt))
+        return bail(fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain: missing carried operator"));
       std::vector<rmc_carry> cy;
       for (auto& c : nd.carry) {  // the top carries only observables
         const int gsite = nd.lo + c.first;
@@ -2342,6 +2802,127 @@ rmc_status solve_chain_core(rmc_ctx* ctx, int n_sites, int L0, int k, int q, int
       for (size_t i = (size_t)qe * len; i < (size_t)q * len; ++i) psi_out[i] = NAN;
     }
   }
+  if (st == RMC_OK && diag) {
+    // one record per merge, children before parents; merges of equal
+    // signature (homogeneous reuse) share their numbers
+    std::vector<int> order;
+    std::function<void(int)> post = [&](int id) {
+      if (nodes[id].left < 0) return;
+      post(nodes[id].left);
+      post(nodes[id].right);
+      order.push_back(id);
+    };
+    post(0);
+    *n_diag = (int)order.size();
+    std::map<std::string, rmc_merge_diag> seen;
+    for (int i = 0; i < (int)order.size() && i < max_diag && st == RMC_OK; ++i) {
+      const int id = order[i];
+      const ChainNode& nd = nodes[id];
+      const rmc_block* A = blk_of[nd.left];
+      const rmc_block* B = blk_of[nd.right];
+      rmc_merge_diag dg{};
+      auto hit = id != 0 ? seen.find(nd.sig) : seen.end();
+      if (hit != seen.end()) {
+        dg = hit->second;
+      } else {
+        dg.kA = A->k;
+        dg.kB = B->k;
+        dg.k = blk_of[id]->k;
+        dg.b = dg.bH = dg.gamma = dg.r = dg.E0 = NAN;
+        st = to_host<double>(ctx, blk_of[id]->E, &dg.a, 1);
+        std::vector<rmc_term> mt;
+        if (st == RMC_OK && !merge_terms_of(id, &mt))
+          st = fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_bounds: missing carried operator");
+        bool avail = false;
+        std::string why;
+        const int L = nd.hi - nd.lo;
+        const int LA = nodes[nd.left].hi - nodes[nd.left].lo, LB = nodes[nd.right].hi - nodes[nd.right].lo;
+        const bool all_kept = LA < 31 && LB < 31 && A->k == (1L << LA) && B->k == (1L << LB);
+        if (all_kept) {  // P = I: b vanishes exactly (its Kronecker form would leave rounding)
+          dg.b = 0.0;
+          avail = true;
+        } else if (st == RMC_OK) {
+          st = coupling_norm(ctx, A, B, mt.data(), (int)mt.size(), &dg.b, &avail, &why);
+        }
+        std::vector<FullTerm> ft = block_full_terms(terms, nd.lo, nd.hi);
+        bool real_terms = true;
+        for (const FullTerm& f : ft) real_terms = real_terms && std::isfinite(f.coef);
+        if (st == RMC_OK && L <= diag_sites && real_terms) {
+          Workspace wd(ctx);
+          FullSpace fs;
+          fs.L = L;
+          fs.dim = 1L << L;
+          fs.nt = (int)ft.size();
+          fs.kA = A->k;
+          fs.kB = B->k;
+          fs.LA = LA;
+          fs.LB = LB;
+          FullTerm* dterms = nullptr;
+          double *UA = nullptr, *UB = nullptr;
+          st = wd.get(&dterms, std::max<size_t>(1, ft.size()));
+          if (st == RMC_OK && !ft.empty() &&
+              (cudaMemcpyAsync(dterms, ft.data(), sizeof(FullTerm) * ft.size(), cudaMemcpyHostToDevice,
+                               ctx->stream) != cudaSuccess ||
+               cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+            st = fail(ctx, RMC_ERR_CUDA, "rmc_solve_chain_bounds: copy of the block terms failed");
+          if (st == RMC_OK) st = lift_block(ctx, wd, nodes, blk_of, nd.left, A->k, &UA);
+          if (st == RMC_OK) st = lift_block(ctx, wd, nodes, blk_of, nd.right, B->k, &UB);
+          fs.terms = dterms;
+          fs.UA = UA;
+          fs.UB = UB;
+          double *f1 = nullptr, *f2 = nullptr;
+          if (st == RMC_OK) st = wd.get(&f1, (size_t)fs.dim);
+          if (st == RMC_OK) st = wd.get(&f2, (size_t)fs.dim);
+          auto whole = [&](double*, double*) -> rmc_status { return RMC_OK; };
+          auto in_q = [&](double* x, double* tmp) -> rmc_status {  // x <- Q x
+            TRY(project_q(ctx, fs, x, tmp));
+            CK(cudaMemcpyAsync(x, tmp, sizeof(double) * fs.dim, cudaMemcpyDeviceToDevice, ctx->stream));
+            return RMC_OK;
+          };
+          // E0 = lambda_min(H) on the block's whole space
+          auto h_apply = [&](const double* x, double* y) -> rmc_status {
+            full_apply_kernel<<<grid1d(fs.dim), 256, 0, ctx->stream>>>(fs.terms, fs.nt, fs.dim, x, y);
+            CKL();
+            return RMC_OK;
+          };
+          if (st == RMC_OK) st = krylov_lowest(ctx, fs.dim, fs.dim, 1e-9, h_apply, whole, &dg.E0);
+          // lambda_min(Q H Q) on range(Q)
+          auto qhq_apply = [&](const double* x, double* y) -> rmc_status {
+            TRY(project_q(ctx, fs, x, f1));
+            TRY(h_apply(f1, f2));
+            TRY(project_q(ctx, fs, f2, y));
+            return RMC_OK;
+          };
+          const long nr = (long)A->k * B->k, dq = fs.dim - nr;
+          double lq = INFINITY;
+          if (st == RMC_OK && dq > 0) st = krylov_lowest(ctx, fs.dim, dq, 1e-9, qhq_apply, in_q, &lq);
+          // ||P H Q||_2^2 = lambda_max(W^T H Q H W) on the retained product
+          // sector (W = U_A (x) U_B): the lowest eigenvalue of its negative
+          auto phq_apply = [&](const double* x, double* y) -> rmc_status {
+            TRY(lift_product(ctx, fs, x, f1));
+            TRY(h_apply(f1, f2));
+            TRY(project_q(ctx, fs, f2, f1));
+            TRY(h_apply(f1, f2));
+            TRY(restrict_product(ctx, fs, f2, y, -1.0));
+            return RMC_OK;
+          };
+          double mb = 0.0;
+          if (st == RMC_OK && dq > 0) st = krylov_lowest(ctx, nr, nr, 1e-9, phq_apply, whole, &mb);
+          if (st == RMC_OK) {
+            dg.bH = dq > 0 ? std::sqrt(std::max(0.0, -mb)) : 0.0;
+            dg.gamma = lq - dg.a;
+            if (dg.bH == 0.0 || std::isinf(dg.gamma)) dg.r = 0.0;
+            else dg.r = 0.5 * (std::sqrt(dg.gamma * dg.gamma + 4.0 * dg.bH * dg.bH) - dg.gamma);
+          }
+        }
+        if (id != 0) seen[nd.sig] = dg;
+      }
+      dg.lo = nd.lo;
+      dg.mid = nodes[nd.left].hi;
+      dg.hi = nd.hi;
+      diag[i] = dg;
+    }
+  }
   cleanup();
   if (st != RMC_OK) return st;
   if (soft != RMC_OK) return fail(ctx, soft, "rmc_solve_chain: a merge did not converge");
@@ -2365,6 +2946,100 @@ extern "C" rmc_status rmc_solve_chain_states(rmc_ctx* ctx, const rmc_chain* c, i
   return solve_chain_core(ctx, c->n_sites, c->L0, c->k, c->q, c->n_onsite, c->onsite_site, c->onsite_pauli,
                           c->onsite_coef, c->n_bonds, c->bond_i, c->bond_j, c->bond_pauli_i, c->bond_pauli_j,
                           c->bond_coef, n_obs, obs, E_out, obs_out, psi_out);
+}
+
+extern "C" rmc_status rmc_solve_chain_bounds(rmc_ctx* ctx, const rmc_chain* c, int full_space_sites,
+                                             int max_merges, rmc_merge_diag* diag, int* n_merges, double* E_out) {
+  if (!ctx) return RMC_ERR_INVAL;
+  if (!c || !n_merges || max_merges < 0 || (max_merges > 0 && !diag))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_bounds: bad arguments");
+  if (full_space_sites > kMaxFullSpaceSites)
+    return fail(ctx, RMC_ERR_INVAL, "rmc_solve_chain_bounds: full-space evaluation needs <= %d sites",
+                kMaxFullSpaceSites);
+  std::vector<double> E(std::max(1, c->q));
+  rmc_status st = solve_chain_core(ctx, c->n_sites, c->L0, c->k, c->q, c->n_onsite, c->onsite_site, c->onsite_pauli,
+                                   c->onsite_coef, c->n_bonds, c->bond_i, c->bond_j, c->bond_pauli_i,
+                                   c->bond_pauli_j, c->bond_coef, 0, nullptr, E_out ? E_out : E.data(), nullptr,
+                                   nullptr, std::max(0, full_space_sites), max_merges, diag ? diag : nullptr,
+                                   n_merges);
+  return st;
+}
+
+extern "C" rmc_status rmc_merge_bound(rmc_ctx* ctx, const rmc_block* A, const rmc_block* B, const rmc_term* terms,
+                                      int n_terms, double* b_out) {
+  TRY(check_ctx(ctx));
+  if (!A || !B || !b_out || n_terms < 0 || (n_terms > 0 && !terms))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_merge_bound: bad arguments");
+  for (int t = 0; t < n_terms; ++t)
+    if (terms[t].op_a < 0 || terms[t].op_a >= A->n_ops || terms[t].op_b < 0 || terms[t].op_b >= B->n_ops ||
+        !std::isfinite(terms[t].coef))
+      return fail(ctx, RMC_ERR_INVAL, "rmc_merge_bound: term %d names no carried operator", t);
+  bool avail = false;
+  std::string why;
+  TRY(coupling_norm(ctx, A, B, terms, n_terms, b_out, &avail, &why));
+  if (!avail) return fail(ctx, RMC_ERR_INVAL, "rmc_merge_bound: %s", why.c_str());
+  return RMC_OK;
+}
+
+extern "C" rmc_status rmc_autotune(rmc_ctx* ctx, const rmc_chain* c, double* E_out) {
+  if (!ctx) return RMC_ERR_INVAL;
+  if (!c) return fail(ctx, RMC_ERR_INVAL, "rmc_autotune: no chain");
+  TuneTable& tt = tune_table();
+  tt.tuning.fetch_add(1);
+  // merges one at a time, so each candidate is timed on an otherwise idle stream
+  const int lanes = ctx->cfg.lanes;
+  ctx->cfg.lanes = 1;
+  std::vector<double> E(std::max(1, c->q));
+  const rmc_status st = solve_chain_core(ctx, c->n_sites, c->L0, c->k, c->q, c->n_onsite, c->onsite_site,
+                                         c->onsite_pauli, c->onsite_coef, c->n_bonds, c->bond_i, c->bond_j,
+                                         c->bond_pauli_i, c->bond_pauli_j, c->bond_coef, 0, nullptr,
+                                         E_out ? E_out : E.data(), nullptr, nullptr);
+  ctx->cfg.lanes = lanes;
+  tt.tuning.fetch_sub(1);
+  return st;
+}
+
+extern "C" size_t rmc_tune_dump(char* buf, size_t len) {
+  TuneTable& tt = tune_table();
+  std::string text;
+  {
+    std::lock_guard<std::mutex> lk(tt.mu);
+    for (const auto& kv : tt.choice) text += kv.first + "=" + std::to_string(kv.second) + "\n";
+  }
+  if (buf && len > 0) {
+    const size_t n = std::min(len - 1, text.size());
+    std::memcpy(buf, text.data(), n);
+    buf[n] = '\0';
+  }
+  return text.size() + 1;
+}
+
+extern "C" int rmc_tune_load(const char* text) {
+  if (!text) return -1;
+  TuneTable& tt = tune_table();
+  std::lock_guard<std::mutex> lk(tt.mu);
+  int count = 0;
+  const char* p = text;
+  while (*p) {
+    const char* e = std::strchr(p, '\n');
+    const std::string line = e ? std::string(p, e - p) : std::string(p);
+    p = e ? e + 1 : p + line.size();
+    if (line.empty()) continue;
+    const size_t eq = line.rfind('=');
+    if (eq == std::string::npos || eq == 0 || eq + 1 >= line.size()) return -1;
+    char* end = nullptr;
+    const long v = std::strtol(line.c_str() + eq + 1, &end, 10);
+    if (!end || *end != '\0' || v < 0 || v > 64) return -1;
+    tt.choice[line.substr(0, eq)] = (int)v;
+    ++count;
+  }
+  return count;
+}
+
+extern "C" void rmc_tune_clear(void) {
+  TuneTable& tt = tune_table();
+  std::lock_guard<std::mutex> lk(tt.mu);
+  tt.choice.clear();
 }
 
 // ---------------------------------------------------------------------------
