@@ -129,13 +129,14 @@ void* rmc_stream(const rmc_ctx* ctx);
 
 /* Opt-in timing of the hot-path kernels on the context stream (CUDA events
  * around every launch group, harvested at the next host synchronisation).
- * Kinds: 0 Kronecker-form product in the working precision of the subspace
- * iteration (FP32 for the mixed paths), 1 Kronecker-form product in FP64,
- * 2 small eigensolver (Jacobi + refinement), 3 Cholesky-QR, 4 Gram products,
- * 5 basis combinations, 6 operator rotation.  rmc_profile_read returns the
- * totals since the last read (launch groups, milliseconds, algorithmic
- * FLOPs) and resets them. */
-#define RMC_PROF_KINDS 7
+ * Kinds: 0 two-stage Kronecker-form product in the working precision of the
+ * subspace iteration (FP32 for the mixed paths), 1 Kronecker-form product in
+ * FP64 (either form), 2 small eigensolver (Jacobi + refinement), 3
+ * Cholesky-QR, 4 Gram products, 5 basis combinations, 6 operator rotation,
+ * 7 single-launch (fused) Chebyshev filter or product in the working
+ * precision.  rmc_profile_read returns the totals since the last read (launch
+ * groups, milliseconds, algorithmic FLOPs) and resets them. */
+#define RMC_PROF_KINDS 8
 rmc_status rmc_profile(rmc_ctx* ctx, int enable);
 rmc_status rmc_profile_read(rmc_ctx* ctx, int kind, uint64_t* groups, uint64_t* launches, double* ms,
                             double* flops);

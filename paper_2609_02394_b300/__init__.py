@@ -33,7 +33,7 @@ EXPORTED = [
     "rmc_couple_batch", "rmc_merge_bound", "rmc_solve_chain_bounds", "rmc_autotune", "rmc_tune_dump",
     "rmc_tune_load", "rmc_tune_clear",
 ]
-PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate"]
+PROF_KINDS = ["kron_working", "kron_fp64", "small_eig", "cholqr", "gram", "combine", "rotate", "fused_working"]
 
 
 class RmcError(RuntimeError):

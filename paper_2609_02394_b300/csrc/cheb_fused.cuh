@@ -200,6 +200,229 @@ __global__ void __launch_bounds__(kFusedThreads)
 
 
 // ---------------------------------------------------------------------------
+// FP32 fused filter with k-major operands and 128-bit shared-memory loads.
+//
+// In cta_gemm above a thread's four rows are 16 apart, so every multiply-add
+// step reads eight scalars (and the rows' stride puts two of them in one bank)
+// for sixteen FMAs: the kernel is bound by shared-memory wavefronts at a
+// fraction of the FMA pipe.  Here every operand is stored k-major (row k holds
+// the whole m or n range), a thread owns a 4 x 4 block of adjacent rows and
+// columns, and one k step is one float4 load of A^T, one of B (16 lanes read
+// 256 contiguous bytes, the two row groups of a warp share them) and sixteen
+// FMAs.  Layouts (floats, row strides padded to multiples of 4 so every float4
+// is 16-byte aligned; a stride that is a multiple of 32 gets 4 more, which
+// spreads the transposing loads and stores over the banks):
+//   Y  [b][M1p]            vector v's element (a, b) at b * M1p + v * kA + a
+//   Ts [(j, a)][N2p]       stage-1 output, column v * kB + b
+//   As [(j, a')][kAp]      coef_j A_j[a][a'] at row j * kA + a', column a
+//   Bt [b'][N1p]           B_j[b][b'] at column j * kB + b
+// ---------------------------------------------------------------------------
+struct V4Layout {
+  int M1p, N1p, N2p, kAp;
+  size_t y, ts, as, bt;  // floats per buffer
+  size_t bytes;          // whole dynamic shared memory, reduction scratch included
+};
+
+__host__ __device__ inline int v4_pad(int x) {
+  int p = (x + 3) & ~3;
+  if ((p & 31) == 0) p += 4;
+  return p;
+}
+
+__host__ __device__ inline V4Layout v4_layout(int kA, int kB, int no, int vpc) {
+  V4Layout L;
+  L.M1p = v4_pad(vpc * kA);
+  L.N1p = v4_pad(no * kB);
+  L.N2p = v4_pad(vpc * kB);
+  L.kAp = (kA + 3) & ~3;
+  L.y = (size_t)kB * L.M1p;
+  L.ts = (size_t)no * kA * L.N2p;
+  L.as = (size_t)no * kA * L.kAp;
+  L.bt = (size_t)kB * L.N1p;
+  L.bytes = sizeof(float) * (2 * L.y + L.ts + L.as + L.bt + 32);
+  return L;
+}
+
+// C(m, n) = sum_k At[k * lda + m] * Bk[k * ldb + n] for an M x N output, by all
+// 256 threads of the CTA in 64 x 64 tiles, 4 x 4 adjacent outputs a thread.
+// lda and ldb are multiples of 4; a float4 whose first row (column) is in
+// range lies wholly inside the padded row, and out-of-range blocks read zeros.
+template <class Epi>
+__device__ __forceinline__ void cta_gemm_v4(int M, int N, int K, const float* At, int lda, const float* Bk, int ldb,
+                                            const Epi& epi) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int m0 = 0; m0 < M; m0 += 64) {
+    for (int n0 = 0; n0 < N; n0 += 64) {
+      const int mr = m0 + 4 * ty, nc = n0 + 4 * tx;
+      const bool am = mr < M, bn = nc < N;
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      const float4* ap = reinterpret_cast<const float4*>(At + mr);
+      const float4* bp = reinterpret_cast<const float4*>(Bk + nc);
+      const int sa = lda >> 2, sb = ldb >> 2;
+#pragma unroll 4
+      for (int k = 0; k < K; ++k) {
+        const float4 a = am ? ap[k * sa] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = bn ? bp[k * sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      if (am && bn) epi.block(mr, nc, M, N, acc);
+    }
+  }
+}
+
+// The epilogues take a thread's whole 4 x 4 block (rows m0.., columns n0..,
+// clipped to M x N) and split m and n into their (vector, index) parts once,
+// stepping them across the block.
+struct V4Epi1 {  // Ts[(j * kA + a) * N2p + v * kB + b] for m = v * kA + a, n = j * kB + b
+  float* Ts;
+  int kA, kB, N2p;
+  __device__ void block(int m0, int n0, int M, int N, const float (&acc)[4][4]) const {
+    int v = m0 / kA, a = m0 - v * kA;
+    const int j0 = n0 / kB, b0 = n0 - j0 * kB;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (m0 + i < M) {
+        int j = j0, b = b0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (n0 + c < N) Ts[(j * kA + a) * N2p + v * kB + b] = acc[i][c];
+          if (++b == kB) { b = 0; ++j; }
+        }
+      }
+      if (++a == kA) { a = 0; ++v; }
+    }
+  }
+};
+
+struct V4Epi2 {  // Yold <- alpha (acc + (EA[a] + EB[b]) x) + beta x + gamma z at (v, a, b)
+  const float* Ycur;
+  float* Yold;
+  const float* EA;
+  const float* EB;
+  int kA, kB, M1p;
+  float alpha, beta, gamma;
+  __device__ void block(int a0, int n0, int M, int N, const float (&acc)[4][4]) const {
+    const int v0 = n0 / kB, b0 = n0 - v0 * kB;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int a = a0 + i;
+      if (a >= M) break;
+      const float ea = EA[a];
+      int v = v0, b = b0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (n0 + c < N) {
+          const int idx = b * M1p + v * kA + a;
+          const float x = Ycur[idx];
+          float y = alpha * (acc[i][c] + (ea + EB[b]) * x) + beta * x;
+          if (gamma != 0.f) y += gamma * Yold[idx];
+          Yold[idx] = y;
+        }
+        if (++b == kB) { b = 0; ++v; }
+      }
+    }
+  }
+};
+
+// One launch: Out = normalised p(H) X (deg >= 1) or Out = H X (deg == 0), as
+// cheb_fused_kernel<float>, with both operators staged in shared memory.
+__global__ void __launch_bounds__(kFusedThreads)
+    cheb_fused_v4_kernel(const float* X, const float* __restrict__ HX, const float* __restrict__ EA,
+                         const float* __restrict__ EB, const float* __restrict__ Acat,
+                         const float* __restrict__ Bcat, float* Out, FusedArgs p) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  float* sm = reinterpret_cast<float*>(fused_smem);
+  const int kA = p.kA, kB = p.kB, no = p.n_ops;
+  const int n = kA * kB;
+  const int v0 = blockIdx.x * p.vpc;
+  const int nvl = min(p.vpc, p.nv - v0);
+  if (nvl <= 0) return;
+  const V4Layout L = v4_layout(kA, kB, no, p.vpc);
+  float* Yp = sm;
+  float* Yc = Yp + L.y;
+  float* Ts = Yc + L.y;
+  float* As = Ts + L.ts;
+  float* Bt = As + L.as;
+  float* red = Bt + L.bt;
+  const long base = (long)v0 * n;
+  const int cnt = nvl * n;
+  const float s1e = (float)(p.sigma1 / p.e);
+  // zero every buffer once, so the padding a float4 may cover holds finite values
+  for (int i = threadIdx.x; i < (int)(2 * L.y + L.ts + L.as + L.bt); i += blockDim.x) sm[i] = 0.f;
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {  // global (v, a, b) -> Y[b][v kA + a]
+    const int v = i / n, r = i - v * n, a = r / kB, b = r - a * kB;
+    const int idx = b * L.M1p + v * kA + a;
+    const float x = X[base + i];
+    Yp[idx] = x;
+    if (!p.compute_hx && p.deg >= 1) Yc[idx] = s1e * (HX[base + i] - (float)p.c * x);
+  }
+  for (int i = threadIdx.x; i < kA * no * kA; i += blockDim.x) {  // Acat[a][(j, a')] -> As[(j, a')][a]
+    const int a = i / (no * kA), k = i - a * (no * kA);
+    As[k * L.kAp + a] = Acat[i];
+  }
+  for (int i = threadIdx.x; i < no * kB * kB; i += blockDim.x) {  // Bcat[(j, b)][b'] -> Bt[b'][(j, b)]
+    const int r = i / kB, k = i - r * kB;
+    Bt[k * L.N1p + r] = Bcat[i];
+  }
+  __syncthreads();
+  auto product = [&](const float* Ysrc, const V4Epi2& e2) {
+    if (no > 0) {
+      cta_gemm_v4(nvl * kA, no * kB, kB, Ysrc, L.M1p, Bt, L.N1p, V4Epi1{Ts, kA, kB, L.N2p});
+      __syncthreads();
+    }
+    cta_gemm_v4(kA, nvl * kB, no * kA, As, L.kAp, Ts, L.N2p, e2);
+    __syncthreads();
+  };
+  if (p.compute_hx || p.deg == 0) {
+    const float a1 = p.deg == 0 ? 1.f : s1e;
+    const float b1 = p.deg == 0 ? 0.f : (float)(-p.c) * s1e;
+    product(Yp, V4Epi2{Yp, Yc, EA, EB, kA, kB, L.M1p, a1, b1, 0.f});
+  }
+  double sigma = p.sigma1;
+  const double tau = 2.0 / p.sigma1;
+  for (int d = 2; d <= p.deg; ++d) {
+    const double s1 = 1.0 / (tau - sigma);
+    product(Yc, V4Epi2{Yc, Yp, EA, EB, kA, kB, L.M1p, (float)(2 * s1 / p.e), (float)(-2 * s1 * p.c / p.e),
+                       (float)(-sigma * s1)});
+    float* t = Yp;  // the new term was written over the old one
+    Yp = Yc;
+    Yc = t;
+    sigma = s1;
+  }
+  if (p.deg == 0) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const int v = i / n, r = i - v * n, a = r / kB, b = r - a * kB;
+      Out[base + i] = Yc[b * L.M1p + v * kA + a];
+    }
+    return;
+  }
+  for (int v = 0; v < nvl; ++v) {
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int a = i / kB, b = i - a * kB;
+      const float y = Yc[b * L.M1p + v * kA + a];
+      s += y * y;
+    }
+    s = block_sum(s, red);
+    const float inv = s > 0.f ? 1.f / sqrtf(s) : 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int a = i / kB, b = i - a * kB;
+      Out[base + (long)v * n + i] = Yc[b * L.M1p + v * kA + a] * inv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The same fused filter for FP64 data in double-FP32 arithmetic, for the FP64
 // refinement of the mixed paths.  This part's FP64 pipe issues ~1.9 DFMA per
 // clock per SM against 128 FP32 FMAs, so FP64-accurate products are formed on
@@ -235,6 +458,7 @@ __device__ __forceinline__ void cta_gemm_df(int M, int N, int K, const float2* A
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) s[i][j] = t[i][j] = 0.f;
+#pragma unroll 2
       for (int k = 0; k < K; ++k) {
         float2 a[4], b[4];
 #pragma unroll

@@ -546,7 +546,25 @@ bool fused_plan(const KronOp<T>& H, int nv, FusedArgs* p, size_t* smem) {
 template <typename T>
 rmc_status launch_fused(rmc_ctx* ctx, const KronOp<T>& H, const T* X, const T* HX, T* Out, const FusedArgs& p,
                         size_t smem, double flops) {
-  ProfScope ps(ctx, sizeof(T) == 8 ? 1 : 0, flops);
+  ProfScope ps(ctx, sizeof(T) == 8 ? 1 : 7, flops);
+  if constexpr (sizeof(T) == 4) {
+    // the k-major float4 kernel whenever its (padded) layout fits: at most
+    // the planned vectors per CTA, fewer if the padding needs the room
+    if (p.n_ops > 0 && p.ops_in_smem) {
+      FusedArgs q = p;
+      while (q.vpc > 1 && v4_layout(q.kA, q.kB, q.n_ops, q.vpc).bytes > kFusedSmemLimit) --q.vpc;
+      const size_t bytes = v4_layout(q.kA, q.kB, q.n_ops, q.vpc).bytes;
+      if (bytes <= kFusedSmemLimit) {
+        CK(cudaFuncSetAttribute(cheb_fused_v4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kFusedSmemLimit));
+        cheb_fused_v4_kernel<<<ceil_div(q.nv, q.vpc), kFusedThreads, bytes, ctx->stream>>>(
+            (const float*)X, (const float*)HX, (const float*)H.EA, (const float*)H.EB, (const float*)H.Acat,
+            (const float*)H.Bcat, (float*)Out, q);
+        CKL();
+        return RMC_OK;
+      }
+    }
+  }
   // process-wide attribute: raise to the limit once, never lower it
   CK(cudaFuncSetAttribute(cheb_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit));
   cheb_fused_kernel<T><<<ceil_div(p.nv, p.vpc), kFusedThreads, smem, ctx->stream>>>(X, HX, H.EA, H.EB, H.Acat,
