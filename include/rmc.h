@@ -137,6 +137,10 @@ void* rmc_stream(const rmc_ctx* ctx);
  * precision.  rmc_profile_read returns the totals since the last read (launch
  * groups, milliseconds, algorithmic FLOPs) and resets them. */
 #define RMC_PROF_KINDS 8
+/* enable: 0 off, 1 every kind, or RMC_PROFILE_MASK | (bit k for each kind k to
+ * time): each timed launch group costs two event records, so timing only the
+ * kinds of interest keeps the host's launch path as it is without timing. */
+#define RMC_PROFILE_MASK 0x100
 rmc_status rmc_profile(rmc_ctx* ctx, int enable);
 rmc_status rmc_profile_read(rmc_ctx* ctx, int kind, uint64_t* groups, uint64_t* launches, double* ms,
                             double* flops);

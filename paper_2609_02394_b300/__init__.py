@@ -177,6 +177,17 @@ def kron_matvec_noalloc(stream: int, dtype: int, kA: int, kB: int, n_ops: int, n
                                        alpha, beta, gamma)
 
 
+PROFILE_MASK = 0x100
+
+
+def _profile_mode(enable: bool, kinds) -> int:
+    if not enable:
+        return 0
+    if kinds is None:
+        return 1
+    return PROFILE_MASK | sum(1 << PROF_KINDS.index(k) for k in kinds)
+
+
 def tune_dump() -> str:
     """The autotuner's table as text ("key=choice" lines)."""
     lib = load_library()
@@ -286,8 +297,10 @@ class Context:
         self._check(self.lib.rmc_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    def profile(self, enable: bool = True):
-        self._check(self.lib.rmc_profile(self.h, 1 if enable else 0))
+    def profile(self, enable: bool = True, kinds=None):
+        """Time launch groups on the stream: every kind, or only ``kinds``
+        (names from PROF_KINDS)."""
+        self._check(self.lib.rmc_profile(self.h, _profile_mode(enable, kinds)))
 
     def profile_read(self):
         """{kind: (launch groups, kernel launches, ms, algorithmic flops)} since the last read."""
@@ -551,8 +564,8 @@ class Server:
     def last_error(self) -> str:
         return self.lib.rmc_server_last_error(self.h).decode()
 
-    def profile(self, enable: bool = True):
-        self.lib.rmc_server_profile(self.h, 1 if enable else 0)
+    def profile(self, enable: bool = True, kinds=None):
+        self.lib.rmc_server_profile(self.h, _profile_mode(enable, kinds))
 
     def profile_read(self):
         out = {}

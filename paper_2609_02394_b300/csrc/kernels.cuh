@@ -3,6 +3,8 @@
 // driver in rmc.cu; see the comments there for the order.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "gemm.cuh"
 
@@ -444,11 +446,14 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, 
         cs[k] = c; sn[k] = sv; P[k] = p; Q[k] = q;
       }
       __syncthreads();
-      // A <- J^T A J, one 2x2 block per (k, l)
-      for (int k = warp; k < half; k += nw) {
+      // A <- J^T A J, one 2x2 block per (k, l); the half^2 blocks are dealt
+      // to the threads in order (the launch sizes the CTA so they divide
+      // evenly), lanes of a warp on consecutive l
+      for (int e = tid; e < half * half; e += nt) {
+        const int k = e / half, l = e - k * half;
         const int pk = P[k], qk = Q[k];
         const float ck = cs[k], sk = sn[k];
-        for (int l = lane; l < half; l += 32) {
+        {
           const int pl = P[l], ql = Q[l];
           const float cl = cs[l], sl = sn[l];
           const float a00 = A[pk * ld + pl], a01 = A[pk * ld + ql];
@@ -463,9 +468,10 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, 
         }
       }
       // V <- V J
-      for (int row = warp; row < m; row += nw) {
+      for (int e = tid; e < m * half; e += nt) {
+        const int row = e / half, l = e - row * half;
         float* vr = Vs + row * mm;
-        for (int l = lane; l < half; l += 32) {
+        {
           const int pl = P[l], ql = Q[l];
           const float c = cs[l], sv = sn[l];
           const float vp = vr[pl], vq = vr[ql];
@@ -488,6 +494,17 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, 
     w[rank] = (TO)di;
     for (int row = 0; row < m; ++row) V[row * m + rank] = (TO)Vs[row * mm + i];
   }
+}
+
+// Threads for jacobi_kernel on an m x m matrix: the fewest multiples of 32
+// (at most 1024) that give every thread the same number of the (m/2)^2 block
+// updates of a round, up to one.
+inline int jacobi_threads(int m) {
+  const int half = ((m + 1) & ~1) / 2;
+  const int blocks = std::max(1, half * half);
+  const int per = (blocks + 1023) / 1024;
+  const int nt = (blocks + per - 1) / per;
+  return std::min(1024, std::max(64, (nt + 31) / 32 * 32));
 }
 
 inline size_t jacobi_smem_bytes(int m) {

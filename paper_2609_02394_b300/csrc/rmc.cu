@@ -75,7 +75,7 @@ struct rmc_ctx {
   std::set<rmc_block*> blocks;
   int trace = 0;  // RMC_TRACE=1 in the environment: per-iteration convergence lines on stderr
   // opt-in per-kind timing (rmc_profile)
-  bool prof = false;
+  unsigned prof = 0;  // bit k set: launch groups of kind k are timed
   struct Pending { cudaEvent_t a, b; int kind; uint64_t launches; double flops; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -208,7 +208,7 @@ struct ProfScope {
   uint64_t l0;
   cudaEvent_t a = nullptr;
   ProfScope(rmc_ctx* c, int k, double f) : ctx(c), kind(k), flops(f), l0(c->launches) {
-    if (ctx->prof) {
+    if (ctx->prof & (1u << kind)) {
       a = take_event(ctx);
       cudaEventRecord(a, ctx->stream);
     }
@@ -659,7 +659,7 @@ rmc_status jacobi(rmc_ctx* ctx, const TI* S, int m, TO* w, TO* V) {
   // always raise it to the largest size any call can need, never lower it.
   CK(cudaFuncSetAttribute(jacobi_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)jacobi_smem_bytes(kMaxSmallDim)));
-  jacobi_kernel<TI, TO><<<1, 1024, sm, ctx->stream>>>(S, m, w, V, ctx->d_status + 1, 30);
+  jacobi_kernel<TI, TO><<<1, jacobi_threads(m), sm, ctx->stream>>>(S, m, w, V, ctx->d_status + 1, 30);
   CKL();
   return RMC_OK;
 }
@@ -1659,7 +1659,9 @@ rmc_status rmc_stats(const rmc_ctx* ctx, uint64_t* launches, uint64_t* iteration
 
 rmc_status rmc_profile(rmc_ctx* ctx, int enable) {
   if (!ctx) return RMC_ERR_INVAL;
-  ctx->prof = enable != 0;
+  if (enable != 0 && enable != 1 && !(enable & RMC_PROFILE_MASK)) return fail(ctx, RMC_ERR_INVAL, "rmc_profile: bad mode");
+  ctx->prof = enable == 0 ? 0u : enable == 1 ? (1u << RMC_PROF_KINDS) - 1u
+                                             : (unsigned)enable & ((1u << RMC_PROF_KINDS) - 1u);
   return RMC_OK;
 }
 
