@@ -16,6 +16,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librmc.so")
 
+# Concurrent solves (server slots, merge lanes) each run on their own CUDA
+# stream; the driver serves streams through CUDA_DEVICE_MAX_CONNECTIONS
+# hardware queues (8 unless set) and streams sharing a queue run their kernels
+# in order.  The variable is read when the CUDA context is created, so this
+# only takes effect when the package is imported before CUDA is first used.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 RMC_OK, RMC_ERR_INVAL, RMC_ERR_NOMEM, RMC_ERR_NOCONV, RMC_ERR_TIMEOUT, RMC_ERR_CUDA = range(6)
 STATUS_NAMES = {0: "RMC_OK", 1: "RMC_ERR_INVAL", 2: "RMC_ERR_NOMEM", 3: "RMC_ERR_NOCONV",
                 4: "RMC_ERR_TIMEOUT", 5: "RMC_ERR_CUDA"}

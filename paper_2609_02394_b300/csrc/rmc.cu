@@ -39,6 +39,16 @@
 
 using namespace rmc;
 
+// Concurrent solves (server slots, merge lanes) each own a CUDA stream; the
+// driver serves streams through CUDA_DEVICE_MAX_CONNECTIONS hardware queues
+// (8 unless set) and streams that share a queue run their kernels in order, so
+// a long one-CTA kernel of one solve would hold back another.  The driver
+// reads the variable when the CUDA context is created: when the library is
+// loaded before that, it asks for 32 queues, unless the caller set a value.
+__attribute__((constructor)) static void rmc_default_connections() {
+  setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0);
+}
+
 struct rmc_block {
   int k = 0;          // kept states
   int n_ops = 0;      // carried operators
