@@ -206,10 +206,9 @@ __global__ void __launch_bounds__(kFusedThreads)
 // step reads eight scalars (and the rows' stride puts two of them in one bank)
 // for sixteen FMAs: the kernel is bound by shared-memory wavefronts at a
 // fraction of the FMA pipe.  Here every operand is stored k-major (row k holds
-// the whole m or n range), a thread owns a 4 x 4 block of adjacent rows and
-// columns, and one k step is one float4 load of A^T, one of B (16 lanes read
-// 256 contiguous bytes, the two row groups of a warp share them) and sixteen
-// FMAs.  Layouts (floats, row strides padded to multiples of 4 so every float4
+// the whole m or n range), a thread owns a block of adjacent rows and columns,
+// and one k step is one vector load of A^T, one of B and a block of FMAs
+// (cta_gemm_v4).  Layouts (floats, row strides padded to multiples of 4 so every float4
 // is 16-byte aligned; a stride that is a multiple of 32 gets 4 more, which
 // spreads the transposing loads and stores over the banks):
 //   Y  [b][M1p]            vector v's element (a, b) at b * M1p + v * kA + a
@@ -243,49 +242,53 @@ __host__ __device__ inline V4Layout v4_layout(int kA, int kB, int no, int vpc) {
   return L;
 }
 
-// C(m, n) = sum_k At[k * lda + m] * Bk[k * ldb + n] for an M x N output, by all
-// 256 threads of the CTA in 64 x 64 tiles, 4 x 4 adjacent outputs a thread.
-// lda and ldb are multiples of 4; a float4 whose first row (column) is in
-// range lies wholly inside the padded row, and out-of-range blocks read zeros.
+// C(m, n) = sum_k At[k * lda + m] * Bk[k * ldb + n] for an M x N output, by the
+// kV4Threads = 512 threads of the CTA in 64 x 64 tiles: a warp owns four
+// adjacent rows (one float4 of A^T a step, the same for every lane: a
+// broadcast), its lanes two adjacent columns each (one float2 of B; the warp
+// reads 256 contiguous bytes).  Sixteen warps a CTA hide the shared-memory and
+// FMA latency that eight could not.  lda and ldb are multiples of 4; a vector
+// whose first row (column) is in range lies wholly inside the padded row, and
+// out-of-range blocks read zeros.
+constexpr int kV4Threads = 512;
+
 template <class Epi>
 __device__ __forceinline__ void cta_gemm_v4(int M, int N, int K, const float* At, int lda, const float* Bk, int ldb,
                                             const Epi& epi) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int m0 = 0; m0 < M; m0 += 64) {
     for (int n0 = 0; n0 < N; n0 += 64) {
-      const int mr = m0 + 4 * ty, nc = n0 + 4 * tx;
+      const int mr = m0 + 4 * ty, nc = n0 + 2 * tx;
       const bool am = mr < M, bn = nc < N;
-      float acc[4][4];
+      float acc[4][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.f;
       const float4* ap = reinterpret_cast<const float4*>(At + mr);
-      const float4* bp = reinterpret_cast<const float4*>(Bk + nc);
-      const int sa = lda >> 2, sb = ldb >> 2;
+      const float2* bp = reinterpret_cast<const float2*>(Bk + nc);
+      const int sa = lda >> 2, sb = ldb >> 1;
 #pragma unroll 4
       for (int k = 0; k < K; ++k) {
         const float4 a = am ? ap[k * sa] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 b = bn ? bp[k * sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 b = bn ? bp[k * sb] : make_float2(0.f, 0.f);
         const float av[4] = {a.x, a.y, a.z, a.w};
-        const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int i = 0; i < 4; ++i) {
+          acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
+          acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
+        }
       }
       if (am && bn) epi.block(mr, nc, M, N, acc);
     }
   }
 }
 
-// The epilogues take a thread's whole 4 x 4 block (rows m0.., columns n0..,
+// The epilogues take a thread's whole 4 x 2 block (rows m0.., columns n0..,
 // clipped to M x N) and split m and n into their (vector, index) parts once,
 // stepping them across the block.
 struct V4Epi1 {  // Ts[(j * kA + a) * N2p + v * kB + b] for m = v * kA + a, n = j * kB + b
   float* Ts;
   int kA, kB, N2p;
-  __device__ void block(int m0, int n0, int M, int N, const float (&acc)[4][4]) const {
+  __device__ void block(int m0, int n0, int M, int N, const float (&acc)[4][2]) const {
     int v = m0 / kA, a = m0 - v * kA;
     const int j0 = n0 / kB, b0 = n0 - j0 * kB;
 #pragma unroll
@@ -293,7 +296,7 @@ struct V4Epi1 {  // Ts[(j * kA + a) * N2p + v * kB + b] for m = v * kA + a, n = 
       if (m0 + i < M) {
         int j = j0, b = b0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 2; ++c) {
           if (n0 + c < N) Ts[(j * kA + a) * N2p + v * kB + b] = acc[i][c];
           if (++b == kB) { b = 0; ++j; }
         }
@@ -310,7 +313,7 @@ struct V4Epi2 {  // Yold <- alpha (acc + (EA[a] + EB[b]) x) + beta x + gamma z a
   const float* EB;
   int kA, kB, M1p;
   float alpha, beta, gamma;
-  __device__ void block(int a0, int n0, int M, int N, const float (&acc)[4][4]) const {
+  __device__ void block(int a0, int n0, int M, int N, const float (&acc)[4][2]) const {
     const int v0 = n0 / kB, b0 = n0 - v0 * kB;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -319,7 +322,7 @@ struct V4Epi2 {  // Yold <- alpha (acc + (EA[a] + EB[b]) x) + beta x + gamma z a
       const float ea = EA[a];
       int v = v0, b = b0;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 2; ++c) {
         if (n0 + c < N) {
           const int idx = b * M1p + v * kA + a;
           const float x = Ycur[idx];
@@ -335,7 +338,7 @@ struct V4Epi2 {  // Yold <- alpha (acc + (EA[a] + EB[b]) x) + beta x + gamma z a
 
 // One launch: Out = normalised p(H) X (deg >= 1) or Out = H X (deg == 0), as
 // cheb_fused_kernel<float>, with both operators staged in shared memory.
-__global__ void __launch_bounds__(kFusedThreads)
+__global__ void __launch_bounds__(kV4Threads)
     cheb_fused_v4_kernel(const float* X, const float* __restrict__ HX, const float* __restrict__ EA,
                          const float* __restrict__ EB, const float* __restrict__ Acat,
                          const float* __restrict__ Bcat, float* Out, FusedArgs p) {
@@ -440,43 +443,48 @@ __global__ void __launch_bounds__(kFusedThreads)
 // ---------------------------------------------------------------------------
 
 
-// cta_gemm in double-float: C(m, n) = sum_k A(m, k) B(k, n), operands float2.
+// cta_gemm in double-float: C(m, n) = sum_k A(m, k) B(k, n), operands float2,
+// by kDfThreads = 512 threads in 64 x 64 tiles: a warp owns four rows 16 apart
+// (one row a load, so its A operand is a broadcast), its lanes two columns 32
+// apart.  Sixteen warps a CTA: the dependent double-float chains need more
+// warps in flight than the eight of the FP32 kernels.
+constexpr int kDfThreads = 512;
+
 template <class Epi>
 __device__ __forceinline__ void cta_gemm_df(int M, int N, int K, const float2* A, int sam, int sak, const float2* B,
                                             int sbk, int sbn, const Epi& epi) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int m0 = 0; m0 < M; m0 += 64) {
     for (int n0 = 0; n0 < N; n0 += 64) {
-      int ar[4], bc[4];
+      int ar[4], bc[2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        ar[i] = min(m0 + ty + 16 * i, M - 1) * sam;
-        bc[i] = min(n0 + tx + 16 * i, N - 1) * sbn;
-      }
-      float s[4][4], t[4][4];
+      for (int i = 0; i < 4; ++i) ar[i] = min(m0 + ty + 16 * i, M - 1) * sam;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) bc[j] = min(n0 + tx + 32 * j, N - 1) * sbn;
+      float s[4][2], t[4][2];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) s[i][j] = t[i][j] = 0.f;
+        for (int j = 0; j < 2; ++j) s[i][j] = t[i][j] = 0.f;
 #pragma unroll 2
       for (int k = 0; k < K; ++k) {
-        float2 a[4], b[4];
+        float2 a[4], b[2];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = A[ar[i] + k * sak];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = B[k * sbk + bc[j]];
+        for (int j = 0; j < 2; ++j) b[j] = B[k * sbk + bc[j]];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) df_mac(s[i][j], t[i][j], a[i], b[j]);
+          for (int j = 0; j < 2; ++j) df_mac(s[i][j], t[i][j], a[i], b[j]);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int m = m0 + ty + 16 * i;
         if (m >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int n = n0 + tx + 16 * j;
+        for (int j = 0; j < 2; ++j) {
+          const int n = n0 + tx + 32 * j;
           if (n < N) epi(m, n, s[i][j], t[i][j]);
         }
       }
@@ -515,7 +523,7 @@ struct DfEpi2 {  // Yold <- alpha (acc + (EA[a] + EB[b]) x) + beta x + gamma z, 
 // (deg == 0), FP64 in and out, double-float inside.  Ahl (kA x n_ops kA) and
 // Bhl (n_ops kB x kB) are Acat and Bcat split into (hi, lo).  X and Out may
 // be the same array.
-__global__ void __launch_bounds__(kFusedThreads)
+__global__ void __launch_bounds__(kDfThreads)
     cheb_fused_df_kernel(const double* X, const double* __restrict__ EA, const double* __restrict__ EB,
                          const float2* __restrict__ Ahl, const float2* __restrict__ Bhl, double* Out, FusedArgs p) {
   extern __shared__ __align__(16) unsigned char fused_smem[];

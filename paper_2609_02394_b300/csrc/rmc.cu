@@ -567,7 +567,7 @@ rmc_status launch_fused(rmc_ctx* ctx, const KronOp<T>& H, const T* X, const T* H
       if (bytes <= kFusedSmemLimit) {
         CK(cudaFuncSetAttribute(cheb_fused_v4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kFusedSmemLimit));
-        cheb_fused_v4_kernel<<<ceil_div(q.nv, q.vpc), kFusedThreads, bytes, ctx->stream>>>(
+        cheb_fused_v4_kernel<<<ceil_div(q.nv, q.vpc), kV4Threads, bytes, ctx->stream>>>(
             (const float*)X, (const float*)HX, (const float*)H.EA, (const float*)H.EB, (const float*)H.Acat,
             (const float*)H.Bcat, (float*)Out, q);
         CKL();
@@ -640,7 +640,7 @@ rmc_status cheb_fused_df(rmc_ctx* ctx, const KronOp<double>& H, const double* X,
   }
   ProfScope ps(ctx, 1, nv * (double)std::max(1, p.deg) * kron_flops_per_vector(H.kA, H.kB, no));
   CK(cudaFuncSetAttribute(cheb_fused_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit));
-  cheb_fused_df_kernel<<<ceil_div(p.nv, p.vpc), kFusedThreads, smem, ctx->stream>>>(X, H.EA, H.EB, Ahl, Bhl, Out, p);
+  cheb_fused_df_kernel<<<ceil_div(p.nv, p.vpc), kDfThreads, smem, ctx->stream>>>(X, H.EA, H.EB, Ahl, Bhl, Out, p);
   CKL();
   *done = true;
   return RMC_OK;
