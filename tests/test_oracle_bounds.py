@@ -50,3 +50,47 @@ def test_full_retention_and_zero_coupling():
     A, B = _two_leaves(c0, 0, 4, 8, 3)
     d = EB.merge_bound(c0, A, B)
     assert d["b"] < 1e-12 and abs(d["a"] - d["E0"]) < 1e-11
+
+
+# Products of the real single-site Paulis (Y carried as iY): p1 p2 = sign * p.
+PAULI_PRODUCT = {("X", "X"): ("I", 1), ("X", "Y"): ("Z", -1), ("X", "Z"): ("Y", -1),
+                 ("Y", "X"): ("Z", 1), ("Y", "Y"): ("I", -1), ("Y", "Z"): ("X", -1),
+                 ("Z", "X"): ("Y", 1), ("Z", "Y"): ("X", 1), ("Z", "Z"): ("I", 1)}
+
+
+def test_pauli_product_table():
+    """The table the Kronecker form of b rests on, against the matrix products."""
+    for (p1, p2), (p, sign) in PAULI_PRODUCT.items():
+        assert np.array_equal(O.pauli_matrix(p1) @ O.pauli_matrix(p2), sign * O.pauli_matrix(p))
+
+
+@pytest.mark.parametrize("chain", [
+    I.xxz(8, [0.7, 1.1, 0.9, 1.4, 0.6, 1.2, 1.0], 1.0, 4, 6, 4),
+    I.tfim(10, 1.0, 0.7, 5, 4, 4),
+    I.xxz(8, [1.0] * 7, 1.0, 4, 5, 4, fields=[0.3, -1.2, 0.8, 1.9, -0.4, 0.1, -1.5, 0.6]),
+])
+def test_kronecker_form_of_b(chain):
+    """Appendix B's b^2 = lambda_max(P V^2 P - (P V P)^2) assembled in the
+    product basis from the carried operators alone: P V^2 P = sum_{s,t} c_s c_t
+    [O_A^s O_A^t] (x) [O_B^s O_B^t], each same-site product a carried Pauli
+    (up to sign) or the identity, and (P V P)^2 from the projected operators.
+    Equals the dense ||P V Q||_2 of the lifted sector."""
+    mid = chain.n_sites // 2
+    A = O.leaf_block(chain, 0, mid, chain.k)
+    B = O.leaf_block(chain, mid, chain.n_sites, chain.k)
+    terms = O.merge_terms(chain, 0, mid, mid, chain.n_sites)
+    kA, kB = len(A.E), len(B.E)
+    M = np.zeros((kA * kB,) * 2)
+    for cs, (sa, pa), (sb, pb) in terms:
+        for ct, (ta, qa), (tb, qb) in terms:
+            assert sa == ta and sb == tb
+            ra, ga = PAULI_PRODUCT[(pa, qa)]
+            rb, gb = PAULI_PRODUCT[(pb, qb)]
+            mA = np.eye(kA) if ra == "I" else A.ops[(sa, ra)]
+            mB = np.eye(kB) if rb == "I" else B.ops[(sb, rb)]
+            M += cs * ct * ga * gb * np.kron(mA, mB)
+            M -= cs * ct * np.kron(A.ops[(sa, pa)] @ A.ops[(ta, qa)], B.ops[(sb, pb)] @ B.ops[(tb, qb)])
+    b = np.sqrt(max(0.0, np.linalg.eigvalsh(M)[-1]))
+    ref = EB.b_from_products(chain, A, B)
+    assert abs(b - ref) < 1e-10 * max(1.0, ref)
+    assert abs(b - EB.merge_bound(chain, A, B)["b"]) < 1e-10 * max(1.0, ref)   # leaves: ||PHQ|| = ||PVQ||
