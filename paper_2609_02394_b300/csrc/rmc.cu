@@ -680,13 +680,16 @@ rmc_status jacobi(rmc_ctx* ctx, const TI* S, int m, TO* w, TO* V) {
 // at once).
 constexpr int kOASteps = 8;
 
+// The m x m products of the refinement: in the mixed paths in double-float on
+// the FP32 pipe (like their block products), in the FP64 path native FP64.
 template <bool TA, bool TB>
 rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, double* C, double beta,
                          const double* Src, const int* skip) {
   GemmShape s{m, m, m, m, m, 0, 0, 1};
   s.skip = skip;
   EpiAxpby<double> epi{C, Src, m, m, 0, 0, 1.0, beta};
-  gemm_small<double, TA, TB>(A, B, s, 1, epi, ctx->stream);
+  if (fp64_by_df(ctx)) launch_gemm<double, 16, 16, 8, 1, 1, TA, TB, EpiAxpby<double>, true>(A, B, s, 1, epi, ctx->stream);
+  else gemm_small<double, TA, TB>(A, B, s, 1, epi, ctx->stream);
   CKL();
   return RMC_OK;
 }
