@@ -311,7 +311,15 @@ rmc_status tuned_launch(rmc_ctx* ctx, const std::string& key, int ncand, Run&& r
     if (it != tt.choice.end() && it->second >= 0 && it->second < ncand) c = it->second;
   }
   if (c < 0 && may_time && tt.tuning.load() > 0 && ncand > 1) {
-    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    struct Events {  // returned to the context's pool on every exit path
+      rmc_ctx* ctx;
+      cudaEvent_t a, b;
+      ~Events() {
+        ctx->event_pool.push_back(a);
+        ctx->event_pool.push_back(b);
+      }
+    } ev{ctx, take_event(ctx), take_event(ctx)};
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     float best = INFINITY;
     int arg = 0;
     for (int i = 0; i < ncand; ++i) {
@@ -324,8 +332,6 @@ rmc_status tuned_launch(rmc_ctx* ctx, const std::string& key, int ncand, Run&& r
       CK(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) { best = ms; arg = i; }
     }
-    ctx->event_pool.push_back(e0);
-    ctx->event_pool.push_back(e1);
     std::lock_guard<std::mutex> lk(tt.mu);
     tt.choice[key] = arg;
     c = arg;
