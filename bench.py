@@ -261,8 +261,9 @@ def run_reference(args):
     oracle solve of one of the same seeded instances the GPU arm solves (about
     7 s on 16 host cores), so value is measured, not extrapolated."""
     from oracle import rmc_oracle as O
-    world, rank, local, pg = dist_setup()
-    if rank != 0:
+    # rank 0 alone runs it; the others exit without work (no process group:
+    # the oracle needs no collective and no GPU)
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     gold = load_gold()
     seeds = batch_seeds(0, args.batch, gold.keys())
