@@ -181,8 +181,8 @@ rmc_status rmc_build_leaf_pauli(rmc_ctx* ctx, int L, int k,
  *            (largest k' with theta[k'] - theta[k'-1] > tau max(1,|theta[k']|))
  *            unless flags has RMC_COUPLE_TOP.
  *   carry  : which of A's and B's operators to rotate into the new block
- *            (Algorithm 1: "transform the projected boundary operators
- *            required at the next merge"); tags are inherited.
+ *            (Algorithm 1: the carried boundary operators are rotated into
+ *            the merged basis for the next merge); tags are inherited.
  * The lowest eigenpairs are found by Chebyshev-filtered subspace iteration on
  * the Kronecker-form product, then finalised in FP64.  RMC_ERR_NOCONV when
  * max_iter is reached (*out is still produced from the best iterate). */
@@ -506,8 +506,8 @@ rmc_status rmc_kron_matvec_noalloc(void* stream, int dtype, int kA, int kB, int 
  * eigenvector matrix (Ogita-Aishima).  1 <= m <= 160. */
 rmc_status rmc_syev(rmc_ctx* ctx, int m, const double* S, double* w, double* V);
 
-/* Rotation of one carried operator into the merged basis (Algorithm 1:
- * "transform the projected boundary operators"): out = C^T (o (x) I_kB) C
+/* Rotation of one carried operator into the merged basis (Algorithm 1, the
+ * operator transform after each merge): out = C^T (o (x) I_kB) C
  * (side 0) or C^T (I_kA (x) o) C (side 1).  C: kr vectors of kA x kB (device,
  * FP64, vector-major), o: k x k (k = kA or kB), out: kr x kr. */
 rmc_status rmc_rotate_op(rmc_ctx* ctx, int side, int kA, int kB, int kr,

@@ -168,6 +168,18 @@ def rf_heisenberg_n128(seed: int | None = None, k: int = 256) -> Chain:
                name=f"rfheis_N128_k{k}_seed{s}")
 
 
+def rf_heisenberg_pair(seed: int | None = None) -> Chain:
+    """Random-field Heisenberg, 24 sites, Delta = 1, J = 1, h_i ~ U[-2,2], two
+    leaves of 12 sites, k = 256: its one merge couples two 256-state blocks
+    (dimension 65536, three boundary operators), the shape of every merge above
+    the first level of the 128-site chain, with inputs small enough to build
+    densely (4096-dimensional leaves)."""
+    s = seed_for(4) * 10 + 24 if seed is None else seed
+    rng = np.random.default_rng(s)
+    hs = rng.uniform(-2.0, 2.0, size=24)
+    return xxz(24, [1.0] * 23, 1.0, leaf_sites=12, k=256, q=16, fields=hs, name=f"rfheis_N24_L12_k256_seed{s}")
+
+
 def serving_requests(n_requests: int, seed: int | None = None) -> List[Chain]:
     """Mixed request stream: model uniform over {TFIM, XXZ, random field},
     N ~ U{8..128}, k in {16,32,64,128,256}, q ~ U{1..16} capped at k."""

@@ -14,7 +14,9 @@ What it computes, step by step, in the paper's order (Sec. II, Algorithm 1):
    couplings <alpha beta|V|alpha' beta'> = sum coef o_A (x) o_B (Eq. (8)),
    assemble the dense k_A k_B x k_A k_B effective Hamiltonian
    diag(E_A + E_B) + sum coef kron(o_A, o_B) (Eq. (7)), diagonalise it fully
-   (Eq. (10)), keep the lowest states (cut and gauge rules below) and rotate
+   (Eq. (10); above FULL_EIGH_MAX_DIM rows only its lowest k_ret + 1
+   eigenpairs, from LAPACK's dsyevr on the same dense matrix), keep the lowest
+   states (cut and gauge rules below) and rotate
    every carried boundary operator into the new basis,
    o_new = C^T kron(o, I) C or C^T kron(I, o) C.
 3. The top block returns its lowest q eigenpairs.
@@ -196,7 +198,8 @@ class MergeRecord:
     mid: int
     hi: int
     H_eff: Optional[np.ndarray]
-    theta: np.ndarray      # full spectrum of H_eff (ascending)
+    theta: np.ndarray      # spectrum of H_eff (ascending): all of it, or the lowest
+                           # k_ret + 1 above FULL_EIGH_MAX_DIM
     k_ret: int
     k_eff: int
 
@@ -206,6 +209,16 @@ class OracleResult:
     energies: np.ndarray
     top: Block
     merges: List[MergeRecord]
+
+
+def _is_symmetric(H: np.ndarray, atol: float) -> bool:
+    """|H - H^T| <= atol everywhere, checked one row slab at a time."""
+    n = H.shape[0]
+    step = max(1, (1 << 24) // max(1, n))
+    for r in range(0, n, step):
+        if np.max(np.abs(H[r:r + step, :] - H[:, r:r + step].T), initial=0.0) > atol:
+            return False
+    return True
 
 
 def cut_rule(theta: np.ndarray, k_ret: int, tau: float = TAU_DEG) -> int:
@@ -251,12 +264,43 @@ def leaf_block(chain: Chain, lo: int, hi: int, k: int, is_top: bool = False) -> 
 
 def effective_hamiltonian(EA: np.ndarray, EB: np.ndarray, coupling) -> np.ndarray:
     """Eq. (7) written out: diag(E_A[a] + E_B[b]) + sum coef * kron(o_A, o_B),
-    with ``coupling`` a list of (coef, o_A, o_B) in the retained bases."""
+    with ``coupling`` a list of (coef, o_A, o_B) in the retained bases.
+
+    The matrix is filled one row slab at a time: the k_B rows of product
+    states (a, .) are diag(E_A[a] + E_B) on the diagonal block plus
+    sum coef * kron(o_A[a, :], o_B), i.e. the rows a*k_B .. a*k_B + k_B - 1 of
+    the Kronecker products, so no temporary as large as H is ever made (a
+    merge of two 256-state blocks gives a 65536 x 65536 matrix of 34 GB)."""
     kA, kB = len(EA), len(EB)
-    H = np.kron(np.diag(EA), np.eye(kB)) + np.kron(np.eye(kA), np.diag(EB))
-    for coef, oA, oB in coupling:
-        H += coef * np.kron(oA, oB)
+    n = kA * kB
+    H = np.zeros((n, n))
+    for a in range(kA):
+        rows = slice(a * kB, (a + 1) * kB)
+        for coef, oA, oB in coupling:
+            H[rows, :] += coef * np.kron(oA[a:a + 1, :], oB)
+        H[rows, rows] += np.diag(EA[a] + EB)
     return H
+
+
+# Above this dimension a merge computes only the eigenpairs it needs (the
+# lowest k_ret + 1: the kept ones and the one the cut rule compares with).
+FULL_EIGH_MAX_DIM = 4096
+
+
+def lowest_eigenpairs(H: np.ndarray, count: int, full_max: Optional[int] = None):
+    """Eigenvalues (ascending) and eigenvectors of the symmetric H (Eq. (10)).
+
+    Up to ``full_max`` rows: the whole spectrum from LAPACK dsyevd
+    (``numpy.linalg.eigh``), the paper's full dense eigendecomposition.  Larger:
+    the lowest ``count`` pairs from LAPACK dsyevr (``scipy.linalg.eigh`` with
+    ``subset_by_index``) on the same dense matrix -- the same eigenpairs, without
+    the eigenvectors nobody keeps.  H may be overwritten in that case."""
+    n = H.shape[0]
+    lim = FULL_EIGH_MAX_DIM if full_max is None else full_max
+    if n <= lim or count >= n:
+        return np.linalg.eigh(H)
+    import scipy.linalg as sl
+    return sl.eigh(H, subset_by_index=[0, count - 1], driver="evr", overwrite_a=True, check_finite=False)
 
 
 def rotate_operator(C: np.ndarray, o: np.ndarray, side: int, kA: int, kB: int) -> np.ndarray:
@@ -274,14 +318,13 @@ def merge_blocks(chain: Chain, A: Block, B: Block, k: int, is_top: bool,
     n = kA * kB
     H = effective_hamiltonian(A.E, B.E, [(coef, A.ops[ka], B.ops[kb])
                                          for coef, ka, kb in merge_terms(chain, A.lo, A.hi, B.lo, B.hi)])
-    if not np.allclose(H, H.T, atol=1e-12, rtol=0):
+    if not _is_symmetric(H, 1e-12):
         raise AssertionError("effective Hamiltonian is not symmetric")
-    theta, V = np.linalg.eigh(H)
+    k_ret = min(chain.q, n) if is_top else min(k, n)
+    theta, V = lowest_eigenpairs(H.copy() if keep_matrix else H, min(n, k_ret + 1))
     if is_top:
-        k_ret = min(chain.q, n)
         k_eff = k_ret
     else:
-        k_ret = min(k, n)
         k_eff = cut_rule(theta, k_ret)
     C = gauge_fix(V[:, :k_eff])
     ops = {}

@@ -3115,15 +3115,21 @@ rmc_status noalloc_kron(cudaStream_t st, int kA, int kB, int n_ops, int nv, cons
   T* Tbuf = (T*)(scratch + acat_bytes);
   Coefs cf{};
   for (int j = 0; j < n_ops; ++j) cf.c[j] = coef[j];
+  // the caller's pending error state was checked on entry, so an error read
+  // here comes from the launch just made
   if (n_ops > 0) {
     build_acat_kernel<T><<<grid1d((long)kA * kA * n_ops), 256, 0, st>>>(A, cf, kA, n_ops, Acat);
+    if (cudaGetLastError() != cudaSuccess) return RMC_ERR_CUDA;
     GemmShape s1{nv * kA, n_ops * kB, kB, kB, kB, 0, 0, 1};
     EpiKron1<T> e1{Tbuf, kA, kB, nv};
     gemm_big<T, false, true>(X, B, s1, 1, e1, st);
+    if (cudaGetLastError() != cudaSuccess) return RMC_ERR_CUDA;
     GemmShape s2{kA, nv * kB, n_ops * kA, (long)n_ops * kA, (long)nv * kB, 0, 0, 1};
     EpiKron2<T> e2{X, Z, EA, EB, Y, kA, kB, (T)alpha, (T)beta, (T)gamma};
     gemm_big<T, false, false>(Acat, Tbuf, s2, 1, e2, st);
   } else {
+    // no coupling terms: a K = 0 product whose epilogue forms D o X (the A
+    // operand is never read)
     GemmShape s0{kA, nv * kB, 0, 1, (long)nv * kB, 0, 0, 1};
     EpiKron2<T> e2{X, Z, EA, EB, Y, kA, kB, (T)alpha, (T)beta, (T)gamma};
     gemm_big<T, false, false>(EA, X, s0, 1, e2, st);
@@ -3143,6 +3149,9 @@ extern "C" rmc_status rmc_kron_matvec_noalloc(void* stream, int dtype, int kA, i
   const size_t need = ((elt * (size_t)std::max(1, n_ops) * kA * kA + 255) / 256) * 256 +
                       elt * (size_t)std::max(1, n_ops) * kA * kB * nv;
   if (need > (size_t)RMC_NOALLOC_SCRATCH_BYTES) return RMC_ERR_NOMEM;
+  // an error the caller left pending is reported, not cleared, and nothing
+  // is launched on top of it
+  if (cudaPeekAtLastError() != cudaSuccess) return RMC_ERR_CUDA;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoallocMaxDevices) return RMC_ERR_CUDA;
   void* scratch = nullptr;

@@ -269,15 +269,17 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs g, Ep
         }
         mma_commit(&mbar);
       }
-      // every thread waits for the MMAs (they read this group's A tiles)
+      // every thread waits for the MMAs (they read this group's A tiles); the
+      // threads start waiting at different times, so the outcome is combined
+      // over the block before anyone acts on it: every thread then takes the
+      // same branch and meets the same barriers
       const bool done = mbar_wait(&mbar, phase, 1u << 24);
       phase ^= 1u;
-      if (!done) {
+      fence_after_sync();
+      if (!__syncthreads_and(done ? 1 : 0)) {
         if (threadIdx.x == 0 && g.err) atomicExch(g.err, 1);
         ok = false;
       }
-      fence_after_sync();
-      __syncthreads();
     }
     if (!ok) break;
     // epilogue: warp w reads accumulator lanes 32w .. 32w + 31

@@ -7,6 +7,7 @@ or a closed form); nothing comes from the CUDA path.
 import json
 import os
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
@@ -25,6 +26,10 @@ def dump(name, payload):
 def main():
     if "--bench-only" in sys.argv:
         return bench_batch()
+    if "--rfheis-k128" in sys.argv:
+        return rfheis_k128()
+    if "--pair-65536" in sys.argv:
+        return pair_65536()
     c1 = I.tfim_n8()
     r1 = O.solve(c1)
     c1f = I.tfim_n8(); c1f.k = 16
@@ -66,6 +71,47 @@ def bench_batch():
     dump("bench_xxz_n32_k64.json", {
         "source": "oracle (Algorithm 1, dense eigh): XXZ N=32, Delta=1, J_i~U[0.5,1.5] per seed, L0=4, k=64, q=8",
         "instances": batch,
+    })
+
+
+def rfheis_k128():
+    """The 128-site random-field Heisenberg chain at k = 128: fifteen merges of
+    dimension 16384, dense (the lowest k_ret + 1 eigenpairs of each from dsyevr).
+    Takes about an hour on 8 host cores."""
+    t0 = time.time()
+    c = I.rf_heisenberg_n128(k=128)
+    r = O.solve(c)
+    dump("rfheis_n128_k128.json", {
+        "source": "oracle (Algorithm 1, dense H_eff of every merge; lowest k_ret+1 eigenpairs by LAPACK dsyevr "
+                  "above 4096 rows): random-field Heisenberg N=128, h_i~U[-2,2] seed 260904, L0=4, k=128, q=16",
+        "chain": c.to_json(),
+        "energies": r.energies.tolist(),
+        "merges": [[m.lo, m.mid, m.hi, m.k_ret, m.k_eff] for m in r.merges],
+        "theta_low": [m.theta[: m.k_ret + 1].tolist() for m in r.merges],
+        "host_seconds": time.time() - t0,
+    })
+
+
+def pair_65536():
+    """One merge of two 256-state blocks (dimension 65536): the 24-site
+    random-field chain with 12-site leaves.  The leaves are dense 4096 x 4096
+    eigensolves; the merge's dense H_eff (34 GB) gives its lowest 257
+    eigenvalues by dsyevr.  Needs ~40 GB of host memory and about an hour on
+    8 cores."""
+    t0 = time.time()
+    c = I.rf_heisenberg_pair()
+    A = O.leaf_block(c, 0, 12, c.k)
+    B = O.leaf_block(c, 12, 24, c.k)
+    blk, rec = O.merge_blocks(c, A, B, c.k, False)
+    dump("rfheis_pair_n65536.json", {
+        "source": "oracle (leaves: dense eigh of 4096 x 4096; merge: dense 65536 x 65536 H_eff of Eq. (7), lowest "
+                  "257 eigenpairs by LAPACK dsyevr): random-field Heisenberg N=24, L0=12, k=256, seed 2609064",
+        "chain": c.to_json(),
+        "leaf_k": [len(A.E), len(B.E)],
+        "leaf_E0": [float(A.E[0]), float(B.E[0])],
+        "k_ret": rec.k_ret, "k_eff": rec.k_eff,
+        "theta": rec.theta.tolist(),
+        "host_seconds": time.time() - t0,
     })
 
 

@@ -53,6 +53,11 @@ def test_xxz_n32_k64(ctx):
     I.xxz(12, list(np.random.default_rng(1).uniform(0.5, 1.5, 11)), 1.0, 3, 24, 6),
     I.xxz(8, [1.0] * 7, 1.0, 4, 16, 8, fields=[0.5, -1.2, 1.9, 0.1, -0.7, 1.1, -1.8, 0.3]),
     I.tfim(3, 1.0, 0.5, 4, 8, 3),                        # a single leaf is the whole chain
+    # unbalanced trees under truncation (floor/ceil halving; swapping the
+    # halves moves these energies by ~0.1, so parity pins the GPU's tree)
+    I.xxz(11, [1.0] * 10, 1.0, 4, 12, 4, fields=list(np.random.default_rng(3).uniform(-2, 2, 11))),
+    I.xxz(13, list(np.random.default_rng(4).uniform(0.5, 1.5, 12)), 1.0, 4, 10, 4),
+    I.xxz(7, [1.0] * 6, 1.0, 2, 3, 3, fields=list(np.random.default_rng(5).uniform(-2, 2, 7))),
 ])
 def test_chain_matches_oracle(ctx, chain):
     _close(ctx, ctx.solve_chain(chain), O.solve(chain).energies)

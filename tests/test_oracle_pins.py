@@ -235,3 +235,107 @@ def test_retained_fraction_arithmetic():
     (about 4.8 %)."""
     assert round(100 * 4 ** 2 / 2 ** 10, 1) == 1.6
     assert round(100 * 7 ** 2 / 2 ** 10, 1) == 4.8
+
+
+# --- the recursion tree: floor/ceil halving (reading of the unbalanced case) -----------
+
+def _leaves(node):
+    if isinstance(node[0], int):
+        return [node]
+    return _leaves(node[0]) + _leaves(node[1])
+
+
+@pytest.mark.parametrize("N,L0,tree", [
+    # written out by hand: a block of n sites splits into floor(n/2) + ceil(n/2)
+    (7, 2, (((0, 1), (1, 3)), ((3, 5), (5, 7)))),
+    (5, 2, ((0, 2), ((2, 3), (3, 5)))),
+    (11, 4, (((0, 2), (2, 5)), ((5, 8), (8, 11)))),
+    (13, 4, (((0, 3), (3, 6)), ((6, 9), (9, 13)))),
+    (24, 3, ((((0, 3), (3, 6)), ((6, 9), (9, 12))), (((12, 15), (15, 18)), ((18, 21), (21, 24))))),
+    (4, 4, (0, 4)),
+])
+def test_split_tree_hand_written(N, L0, tree):
+    assert O.split_tree(0, N, L0) == tree
+
+
+def test_split_tree_48_sites_leaves_of_three():
+    """N = 48, L0 = 3 (the sweep's longest chains): sixteen 3-site leaves in
+    order, four levels of merges, every merge of two equal halves."""
+    t = O.split_tree(0, 48, 3)
+    assert _leaves(t) == [(3 * i, 3 * i + 3) for i in range(16)]
+    node, depth = t, 0
+    while not isinstance(node[0], int):
+        node, depth = node[0], depth + 1
+    assert depth == 4
+
+
+def test_unbalanced_truncated_energies_depend_on_the_split():
+    """The floor/ceil reading is visible in truncated results: with the halves
+    swapped (ceil first) the 11-site random-field chain keeps different
+    states and its energies move by ~0.1, so the GPU's parity on this chain
+    pins its tree to the oracle's."""
+    rng = np.random.default_rng(3)
+    c = I.xxz(11, [1.0] * 10, 1.0, 4, 12, 4, fields=list(rng.uniform(-2, 2, 11)))
+    base = O.solve(c).energies
+
+    def ceil_first(lo, hi, L0):
+        n = hi - lo
+        if n <= L0:
+            return (lo, hi)
+        mid = lo + (n + 1) // 2
+        return (ceil_first(lo, mid, L0), ceil_first(mid, hi, L0))
+
+    orig = O.split_tree
+    O.split_tree = ceil_first
+    try:
+        swapped = O.solve(c).energies
+    finally:
+        O.split_tree = orig
+    assert np.abs(base - swapped).max() > 1e-3
+
+
+# --- large merges: slab assembly of Eq. (7) and the subset eigensolve ------------------
+
+def test_effective_hamiltonian_matches_dense_definition():
+    """The slab-by-slab assembly equals the Kronecker sum of Eq. (7) built in
+    one piece (a rectangular k_A != k_B case, three terms)."""
+    rng = np.random.default_rng(8)
+    EA, EB, oA, oB, coef = I.random_block_inputs(rng, 5, 7, 3)
+    H = O.effective_hamiltonian(EA, EB, list(zip(coef, oA, oB)))
+    ref = np.kron(np.diag(EA), np.eye(7)) + np.kron(np.eye(5), np.diag(EB))
+    for c, a, b in zip(coef, oA, oB):
+        ref += c * np.kron(a, b)
+    np.testing.assert_allclose(H, ref, atol=1e-14)
+    # element check straight from the product-basis definition (Eq. (5), (8))
+    a, b, ap, bp = 3, 2, 1, 6
+    v = sum(c * oa[a, ap] * ob[b, bp] for c, oa, ob in zip(coef, oA, oB))
+    assert abs(H[a * 7 + b, ap * 7 + bp] - v) < 1e-14
+
+
+def test_subset_eigensolve_equals_full_spectrum():
+    """Above FULL_EIGH_MAX_DIM a merge takes its lowest k_ret + 1 eigenpairs
+    from dsyevr: the same values and (up to sign) vectors as dsyevd, and a
+    merge run both ways keeps the same energies, k_eff and rotated operators."""
+    rng = np.random.default_rng(9)
+    c = I.xxz(12, [1.0] * 11, 1.0, 4, 40, 6, fields=list(rng.uniform(-2, 2, 12)))
+    A = O.leaf_block(c, 0, 6, 40)
+    B = O.leaf_block(c, 6, 12, 40)
+    H = O.effective_hamiltonian(A.E, B.E, [(cf, A.ops[ka], B.ops[kb])
+                                           for cf, ka, kb in O.merge_terms(c, 0, 6, 6, 12)])
+    w_full, V_full = O.lowest_eigenpairs(H.copy(), 41, full_max=10**9)
+    w_sub, V_sub = O.lowest_eigenpairs(H.copy(), 41, full_max=16)
+    assert len(w_sub) == 41
+    np.testing.assert_allclose(w_sub, w_full[:41], atol=1e-11)
+    ov = np.abs(np.sum(V_sub * V_full[:, :41], axis=0))
+    assert np.all(ov > 1 - 1e-8)
+    blk_full, rec_full = O.merge_blocks(c, A, B, 40, False)
+    saved = O.FULL_EIGH_MAX_DIM
+    O.FULL_EIGH_MAX_DIM = 16
+    try:
+        blk_sub, rec_sub = O.merge_blocks(c, A, B, 40, False)
+    finally:
+        O.FULL_EIGH_MAX_DIM = saved
+    assert rec_sub.k_eff == rec_full.k_eff and len(rec_sub.theta) == 41
+    np.testing.assert_allclose(blk_sub.E, blk_full.E, atol=1e-11)
+    for key in blk_full.ops:
+        np.testing.assert_allclose(blk_sub.ops[key], blk_full.ops[key], atol=1e-9)

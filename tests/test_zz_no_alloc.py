@@ -59,3 +59,37 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     st = P.kron_matvec_noalloc(0, 0, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(),
                                d[3].data_ptr(), [1.0, 1.0, 1.0], d[4].data_ptr(), d[5].data_ptr())
     assert st == P.RMC_ERR_NOMEM
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_noalloc_without_coupling_terms(dtype):
+    """n_ops = 0: the product is the diagonal part alone, D o X, scaled and
+    combined with X and Z; the allocation-free call agrees with the regular
+    one on two shapes in a row."""
+    torch = torch_cuda()
+    npdt = np.float64 if dtype == 0 else np.float32
+    tol = 1e-12 if dtype == 0 else 3e-5
+    with P.Context(precision="fp64") as ctx:
+        for call, (kA, kB, nv) in enumerate([(40, 24, 17), (7, 130, 3)]):
+            rng = np.random.default_rng(500 + 10 * dtype + call)
+            EA = np.sort(rng.uniform(-3, 3, kA))
+            EB = np.sort(rng.uniform(-3, 3, kB))
+            X = rng.standard_normal((nv, kA, kB))
+            Z = rng.standard_normal((nv, kA, kB))
+            d = [dev(a, npdt) for a in (EA, EB, X, Z)]
+            Y_ref = dev(np.zeros_like(X), npdt)
+            Y_new = dev(np.full_like(X, np.nan), npdt)
+            torch.cuda.synchronize()
+            ctx.kron_matvec(dtype, kA, kB, 0, nv, d[0].data_ptr(), d[1].data_ptr(), 0, 0, [], d[2].data_ptr(),
+                            Y_ref.data_ptr(), d[3].data_ptr(), 0.5, 0.25, -1.0)
+            torch.cuda.synchronize()
+            st = P.kron_matvec_noalloc(torch.cuda.current_stream().cuda_stream, dtype, kA, kB, 0, nv,
+                                       d[0].data_ptr(), d[1].data_ptr(), 0, 0, [], d[2].data_ptr(),
+                                       Y_new.data_ptr(), d[3].data_ptr(), 0.5, 0.25, -1.0)
+            assert st == P.RMC_OK
+            ref, got = host(Y_ref), host(Y_new)
+            # the definition, element by element: 0.5 (E_A[a] + E_B[b]) X + 0.25 X - Z
+            want = 0.5 * (EA[:, None] + EB[None, :]) * X + 0.25 * X - Z
+            scale = max(1.0, np.abs(want).max())
+            assert np.abs(ref - want).max() <= tol * scale
+            assert np.abs(got - ref).max() <= tol * scale, (call, np.abs(got - ref).max() / scale)
