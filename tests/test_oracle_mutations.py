@@ -47,22 +47,19 @@ def test_dropped_coupling_is_caught(monkeypatch):
 
 def test_transposed_coupling_operand_is_caught(monkeypatch):
     """o_B (x) o_A in place of o_A (x) o_B in the coupling term of Eq. (7)."""
-    real_kron = np.kron
+    real = O.effective_hamiltonian
     calls = {"n": 0}
 
-    class KronSpy:
-        def __getattr__(self, name):
-            return getattr(np, name)
-
-        @staticmethod
-        def kron(a, b):
-            # the coupling term is the only kron of two non-diagonal, non-identity
-            # operators of the same (square) shape class in merge_blocks
-            if a.ndim == 2 and b.ndim == 2 and not _is_diag(a) and not _is_diag(b):
+    def swapped(EA, EB, coupling):
+        out = []
+        for coef, oA, oB in coupling:
+            if oA.shape == oB.shape:
                 calls["n"] += 1
-                return real_kron(b.T, a.T).T if a.shape == b.shape else real_kron(a, b)
-            return real_kron(a, b)
-    monkeypatch.setattr(O, "np", KronSpy())
+                out.append((coef, oB, oA))
+            else:
+                out.append((coef, oA, oB))
+        return real(EA, EB, out)
+    monkeypatch.setattr(O, "effective_hamiltonian", swapped)
     held = _ed_pin_holds()
     assert calls["n"] > 0
     assert not held
