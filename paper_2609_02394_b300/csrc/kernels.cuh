@@ -800,6 +800,35 @@ __global__ void axpby_kernel(const T* __restrict__ P, const T* __restrict__ Q, l
     out[e] = a1 * P[e] + a2 * Q[e];
 }
 
+// Refinement in defect form (the mixed paths' FP64 refinement of wide
+// blocks).  Rf = HC - C diag(w): the Ritz residuals, formed in FP64 and kept
+// in FP32 (they are small; FP32 keeps them to ~6e-8 of their own size).
+__global__ void ritz_residual_kernel(const double* __restrict__ C, const double* __restrict__ HC,
+                                     const double* __restrict__ w, long n, long tot, float* __restrict__ Rf) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    Rf[e] = (float)(HC[e] - w[e / n] * C[e]);
+}
+
+// D[i][r] += s[i] * Rf[i][r]: the source term of the defect recurrence.
+__global__ void add_scaled_columns_kernel(float* __restrict__ D, const float* __restrict__ Rf,
+                                          const float* __restrict__ s, long n, long tot) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    D[e] += s[e / n] * Rf[e];
+}
+
+// X[i][r] = y[i] C[i][r] + D[i][r]: the filtered block, p(H) C = C p(Theta) + D.
+__global__ void defect_combine_kernel(const double* __restrict__ C, const double* __restrict__ y,
+                                      const float* __restrict__ D, long n, long tot, double* __restrict__ X) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    X[e] = y[e / n] * C[e] + (double)D[e];
+}
+
+// Y += F (FP32 addend into FP64).
+__global__ void add_f32_kernel(double* __restrict__ Y, const float* __restrict__ F, long tot) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    Y[e] += (double)F[e];
+}
+
 // F^T for the first-order second Cholesky-QR pass: G = I + E  =>  R ~ I + F,
 // F upper triangular with F_ij = E_ij (i < j), F_ii = E_ii / 2; returns
 // W = F^T (lower triangular) so that X_new = X - W X.

@@ -1300,6 +1300,152 @@ rmc_status prepare_kron(rmc_ctx* ctx, Workspace& ws, const MergeInput& in, KronO
   return RMC_OK;
 }
 
+// FP64 refinement of a wide block (more vectors than the small eigensolver
+// takes) in defect form, for the mixed paths.
+//
+// The iterate is C (FP64, orthonormal Ritz vectors, Ritz values w) together
+// with its FP64-accurate product HC.  A Chebyshev filter pass (the scaled
+// recurrence of cheb_filter, bounds from the current Ritz values) applied to
+// C splits exactly into
+//     p(H) C = C diag(y(w)) + D,
+// where y_d is the same three-term recurrence evaluated at the Ritz values
+// and the defect D obeys
+//     D_1 = (s_1/e) R,
+//     D_d = (2 s_d/e)(H - c) D_{d-1} - s_{d-1} s_d D_{d-2} + (2 s_d/e) R diag(y_{d-1})
+// with R = HC - C diag(w) the Ritz residuals.  D is as small as R, so its
+// products run in FP32 (a rounding error of FP32 relative to D is ~1e-7 of R,
+// far below the FP64 target), and the new block X = C diag(y) + D is FP64-
+// accurate.  After the FP64 orthonormalisation of X, its product is again
+// split: with M = C^T X and Q = X - C M (the part of X outside span C, as
+// small as the subspace moved),
+//     H X = HC M + H Q,
+// HC M in FP64 and H Q in FP32.  So a refinement pass costs FP32 Kronecker
+// products plus FP64-accurate Gram and combination GEMMs; the only
+// FP64-accurate Kronecker product is the first one, of the working-precision
+// block.  The filter covers the whole block at once (no chunks): its
+// amplification ratio is capped (kDefectRho) so that the filtered block stays
+// within ~1e-4 of orthonormal and first-order Cholesky-QR passes suffice, and
+// the Rayleigh-Ritz matrix of the new block is nearly diagonal, so its FP64
+// eigensolver starts from the identity.
+//
+// On return C holds the Ritz vectors and w their values (ascending), the
+// residual test having passed for the first k_acc vectors or max_passes filter
+// passes run.  X, HX and HC are scratch (b x n FP64 each, HC also n_ops wide
+// for the first product), Tf FP32 scratch for the FP32 products.
+constexpr double kDefectRho = 1e5;
+constexpr int kDefectMaxDeg = 40;
+
+rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>& H64, const KronOp<float>& Hf, int b,
+                              int k_acc, double ub, double tol, int max_passes, double* X, double* HX, double* C,
+                              double* HC, double* G, double* w, double* Z, double* rn) {
+  const long n = H64.n();
+  const long tot = (long)b * n;
+  float *Rf, *D0, *D1, *D2, *Tf, *sdev;
+  double *M, *ydev;
+  TRY(ws.get(&Rf, (size_t)tot));
+  TRY(ws.get(&D0, (size_t)tot));
+  TRY(ws.get(&D1, (size_t)tot));
+  TRY(ws.get(&D2, (size_t)tot));
+  TRY(ws.get(&Tf, (size_t)std::max(1, Hf.n_ops) * tot));
+  TRY(ws.get(&sdev, (size_t)kDefectMaxDeg * b));
+  TRY(ws.get(&ydev, (size_t)b));
+  TRY(ws.get(&M, (size_t)b * b));
+  // FP64 Rayleigh-Ritz of the working-precision block: the one FP64-accurate
+  // Kronecker product (HC serves as its scratch before it holds H C)
+  TRY(cholqr64_refine(ctx, ws, X, b, n, C));
+  TRY(kron_product<double>(ctx, H64, X, b, HX, HC));
+  auto rayleigh_ritz = [&]() -> rmc_status {
+    TRY(gram<double>(ctx, ws, X, b, HX, b, n, G, true));
+    TRY(syev64(ctx, ws, G, b, w, Z, true));
+    TRY(combine<double>(ctx, Z, true, b, b, X, n, C, 1.0, 0.0, nullptr));
+    return combine<double>(ctx, Z, true, b, b, HX, n, HC, 1.0, 0.0, nullptr);
+  };
+  TRY(rayleigh_ritz());
+  std::vector<double> th(b), y0(b), y1(b), y2(b);
+  std::vector<float> sc((size_t)kDefectMaxDeg * b);
+  for (int pass = 0;; ++pass) {
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    residual_kernel<double><<<b, 256, 0, ctx->stream>>>(C, HC, w, n, k_acc, tol, rn, ctx->d_status);
+    CKL();
+    int fails = 0;
+    TRY(read_status(ctx, &fails, 1));
+    TRY(to_host<double>(ctx, w, th.data(), b));
+    if (ctx->trace) {
+      std::vector<double> r(b);
+      TRY(to_host<double>(ctx, rn, r.data(), b));
+      int wi = 0;
+      const double worst = worst_relative(r, th, k_acc, &wi);
+      fprintf(stderr, "[rmc refine defect] n=%ld b=%d pass=%d fails=%d worst i=%d res=%.3e theta=%.12g thb=%.12g\n", n,
+              b, pass, fails, wi, worst, th[wi], th[b - 1]);
+    }
+    if (fails == 0 || pass >= max_passes) break;
+    const double a = th[b - 1], e = (ub - a) / 2, c = (ub + a) / 2;
+    if (!(e > 0)) break;
+    const double x0 = std::fabs((th[0] - c) / e);
+    int deg = (int)std::floor(std::acosh(kDefectRho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
+    deg = std::max(2, std::min(kDefectMaxDeg, deg));
+    // scalar recurrence at the Ritz values and the per-column source scales
+    double sigma = e / (th[0] - c);
+    const double tau = 2.0 / sigma;
+    for (int i = 0; i < b; ++i) {
+      y0[i] = 1.0;
+      y1[i] = sigma / e * (th[i] - c);
+    }
+    std::vector<double> s_of(deg + 1);
+    for (int d = 2; d <= deg; ++d) {
+      const double s1 = 1.0 / (tau - sigma);
+      for (int i = 0; i < b; ++i) {
+        sc[(size_t)(d - 2) * b + i] = (float)(2 * s1 / e * y1[i]);
+        y2[i] = 2 * s1 / e * (th[i] - c) * y1[i] - sigma * s1 * y0[i];
+      }
+      std::swap(y0, y1);
+      std::swap(y1, y2);
+      s_of[d] = s1;
+      sigma = s1;
+    }
+    // (pageable sources: the copies are staged before the calls return)
+    CK(cudaMemcpyAsync(sdev, sc.data(), sizeof(float) * (size_t)(deg - 1) * b, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ydev, y1.data(), sizeof(double) * b, cudaMemcpyHostToDevice, ctx->stream));
+    // defect recurrence in FP32
+    ritz_residual_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(C, HC, w, n, tot, Rf);
+    CKL();
+    CK(cudaMemsetAsync(D0, 0, sizeof(float) * tot, ctx->stream));
+    sigma = e / (th[0] - c);
+    axpby_kernel<float><<<grid1d(tot), 256, 0, ctx->stream>>>(Rf, Rf, tot, (float)(sigma / e), 0.0f, D1);
+    CKL();
+    float *Dp = D0, *Dc = D1, *Dn = D2;
+    for (int d = 2; d <= deg; ++d) {
+      const double s1 = s_of[d];
+      TRY(kron_work<float>(ctx, Hf, Dc, b, Dn, (float)(2 * s1 / e), (float)(-2 * s1 * c / e), (float)(-sigma * s1), Dp,
+                           Tf));
+      add_scaled_columns_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(Dn, Rf, sdev + (size_t)(d - 2) * b, n, tot);
+      CKL();
+      float* t = Dp;
+      Dp = Dc;
+      Dc = Dn;
+      Dn = t;
+      sigma = s1;
+    }
+    // X = C diag(y) + D, normalised, orthonormalised in FP64
+    defect_combine_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(C, ydev, Dc, n, tot, X);
+    CKL();
+    normalize_kernel<double><<<b, 256, 0, ctx->stream>>>(X, n, nullptr);
+    CKL();
+    TRY(cholqr64_refine(ctx, ws, X, b, n, HX));
+    // H X = HC M + H Q with M = C^T X, Q = X - C M (Q in FP32 for its product)
+    TRY(gram<double>(ctx, ws, C, b, X, b, n, M, false));
+    TRY(combine<double>(ctx, M, true, b, b, C, n, HX, -1.0, 1.0, X));
+    convert_kernel<float, double><<<grid1d(tot), 256, 0, ctx->stream>>>(HX, D0, tot);
+    CKL();
+    TRY(kron_work<float>(ctx, Hf, D0, b, D1, 1.0f, 0.0f, 0.0f, nullptr, Tf));
+    TRY(combine<double>(ctx, M, true, b, b, HC, n, HX, 1.0, 0.0, nullptr));
+    add_f32_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(HX, D1, tot);
+    CKL();
+    TRY(rayleigh_ritz());
+  }
+  return RMC_OK;
+}
+
 template <typename W>
 rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_status* soft) {
   Workspace ws(ctx);
@@ -1366,6 +1512,7 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   bool converged = true;
   int iters = 0;
   std::vector<double> th_work;  // working-precision Ritz values (mixed paths)
+  KronOp<W> Hw;                 // working-precision operator (mixed paths)
   const bool dense = (b == n) && !chunked;
   if (dense) {
     CK(cudaMemsetAsync(X64, 0, sizeof(double) * b * n, ctx->stream));
@@ -1383,7 +1530,6 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
         TRY((chfsi<double>(ctx, ws, H64, b, k_conv, idx, ub, tol, ctx->cfg.max_iter, X64, HX64, th, &iters,
                            &converged)));
     } else {
-      KronOp<W> Hw;
       TRY(prepare_kron<W>(ctx, ws, in, &Hw));
       W *Xw, *HXw, *thw;
       TRY(ws.get(&Xw, (size_t)b * n));
@@ -1421,6 +1567,7 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   // a locked block takes the chunk orthonormalisation once, without filter.
   const int bf = b;
   constexpr int kRefinePasses = 4;
+  constexpr int kDefectPasses = 8;
   constexpr double kRefineTol = 1e-8;
   const bool refine = sizeof(W) == 4 && !dense && th_work.size() == (size_t)bf;
   std::vector<double> th_cur = th_work;
@@ -1430,7 +1577,18 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   TRY(ws.get(&Zs, (size_t)bf * bf));
   TRY(ws.get(&rn64, bf));
   double* C = tmp64;
-  for (int pass = 0;; ++pass) {
+  const int k_acc = std::min(k_conv, k_ret);
+  bool defect_done = false;
+  if constexpr (sizeof(W) == 4) {
+    if (chunked && refine) {
+      // wide block: refinement in defect form (FP32 products on the small
+      // defect, FP64-accurate Gram and combination GEMMs)
+      TRY(refine_wide_defect(ctx, ws, H64, Hw, bf, k_acc, ub, kRefineTol, kDefectPasses, X64, HX64, C, Tb64, Gs, w,
+                             Zs, rn64));
+      defect_done = true;
+    }
+  }
+  for (int pass = 0; !defect_done; ++pass) {
     if (chunked) {
       const int cw = 128;
       Workspace wc(ctx);
@@ -1508,8 +1666,7 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
     // only the kept vectors need the FP64 accuracy; the extra one beyond them
     // serves the cut rule, whose gap test needs its Ritz value only, and that
-    // is accurate to the square of its residual
-    const int k_acc = std::min(k_conv, k_ret);
+    // is accurate to the square of its residual (k_acc)
     residual_kernel<double><<<bf, 256, 0, ctx->stream>>>(C, HC, w, n, k_acc, kRefineTol, rn64, ctx->d_status);
     CKL();
     int fails = 0;
