@@ -76,6 +76,24 @@ struct EpiKron1T {  // m = v*kA + a, n = j*kB + b  ->  T'[(v*kB + b)*(n_ops*kA) 
     const int v = m / kA, a = m % kA, j = n / kB, b = n % kB;
     Tbuf[((long)v * kB + b) * ((long)n_ops * kA) + (long)j * kA + a] = acc;
   }
+  // cnt (<= 32) consecutive columns n0 .. n0 + cnt - 1 of row m: the index
+  // arithmetic once per run, then (j, b) stepped
+  __device__ void run(int m, int n0, const float (&val)[32], int cnt) const {
+    const int v = m / kA, a = m % kA;
+    int j = n0 / kB, b = n0 % kB;
+    const long ld = (long)n_ops * kA;
+    T* base = Tbuf + (long)v * kB * ld + a;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) {
+        base[(long)b * ld + (long)j * kA] = (T)val[t];
+        if (++b == kB) {
+          b = 0;
+          ++j;
+        }
+      }
+    }
+  }
 };
 
 template <typename T>
@@ -94,6 +112,29 @@ struct EpiKron2T {  // m = v*kB + b, n = a
     T y = alpha * (acc + (EA[n] + EB[b]) * x) + beta * x;
     if (gamma != T(0)) y += gamma * Z[idx];
     Y[idx] = y;
+  }
+  // cnt (<= 32) consecutive columns a = n0 .. n0 + cnt - 1 of row (v, b).
+  // Every input of the run is loaded before the first store, so the loads
+  // overlap (a store to Y could otherwise alias a later X load and serialise
+  // them on the memory latency).
+  __device__ void run(int m, int n0, const float (&val)[32], int cnt) const {
+    const int v = m / kB, b = m % kB;
+    const T eb = __ldg(EB + b);
+    const long idx0 = ((long)v * kA + n0) * kB + b;
+    T x[32], z[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      x[t] = t < cnt ? __ldg(X + idx0 + (long)t * kB) : T(0);
+      z[t] = (gamma != T(0) && t < cnt) ? __ldg(Z + idx0 + (long)t * kB) : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < cnt) {
+        T y = alpha * ((T)val[t] + (__ldg(EA + n0 + t) + eb) * x[t]) + beta * x[t];
+        if (gamma != T(0)) y += gamma * z[t];
+        Y[idx0 + (long)t * kB] = y;
+      }
+    }
   }
 };
 

@@ -35,6 +35,7 @@
 #include "cheb_fused.cuh"
 #include "kernels.cuh"
 #include "umma.cuh"
+#include "tma_gemm.cuh"
 #include "bounds.cuh"
 
 using namespace rmc;
@@ -493,10 +494,15 @@ rmc_status kron_apply(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y
 // Kronecker-form product on the tcgen05 tensor cores (3xTF32, FP32 data).
 // Returns false (and launches nothing) when a stage's shape does not fit the
 // tensor-core kernel; the caller then runs the SIMT product.
+bool tma_fits(long lda, long ldb, int K);
 bool tc_fits(int kA, int kB, int n_ops) {
   int np, g;
   size_t sm;
-  return n_ops > 0 && umma::plan(n_ops * kB, kB, &np, &g, &sm) && umma::plan(kA, n_ops * kA, &np, &g, &sm);
+  if (n_ops <= 0) return false;
+  // each stage on the TMA-fed kernel (any N) or the plain-load one (N <= 256)
+  const bool s1 = tma_fits(kB, kB, kB) || umma::plan(n_ops * kB, kB, &np, &g, &sm);
+  const bool s2 = tma_fits((long)n_ops * kA, (long)n_ops * kA, n_ops * kA) || umma::plan(kA, n_ops * kA, &np, &g, &sm);
+  return s1 && s2;
 }
 
 template <class Epi>
@@ -515,13 +521,110 @@ rmc_status launch_tc(rmc_ctx* ctx, const float* A, long lda, int M, const float*
   return RMC_OK;
 }
 
+// TMA-fed pipelined form (tma_gemm.cuh).  The tensor-map encoder is a
+// driver entry point, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+
+// Tensor map of a K-contiguous FP32 matrix (rows x K, row pitch ld floats),
+// box 32 x box_rows, 128-byte swizzle, zero fill out of bounds.  False when
+// the TMA cannot address it (pitch not a multiple of 16 bytes, base not
+// 16-byte aligned).
+bool make_map(CUtensorMap* m, const float* ptr, long rows, long K, long ld, int box_rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || ((uintptr_t)ptr & 15) || (ld % 4) != 0 || K < 1 || rows < 1 || ld < K) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 148;
+    return v > 0 ? v : 148;
+  }();
+  return n;
+}
+
+// N tiling of the TMA kernel: at most max_bn (256, or 128 for the deeper
+// pipeline) columns a tile, the columns dealt evenly over the tiles, rounded
+// up to the MMA's multiple of 16.
+int tma_max_bn() {
+  static int v = [] {
+    const char* e = std::getenv("RMC_TMA_BN");
+    const int b = e ? std::atoi(e) : 256;
+    return b == 128 ? 128 : 256;
+  }();
+  return v;
+}
+
+inline void tma_n_tiles(int N, int* n_tiles, int* BN) {
+  const int mx = tma_max_bn();
+  *n_tiles = (N + mx - 1) / mx;
+  *BN = ((N + *n_tiles - 1) / *n_tiles + 15) / 16 * 16;
+}
+
+bool tma_fits(long lda, long ldb, int K) { return encode_tiled() && K >= 1 && lda % 4 == 0 && ldb % 4 == 0; }
+
+template <class Epi>
+rmc_status launch_tma(rmc_ctx* ctx, const float* A, long lda, int M, const float* B, long ldb, int N, int K,
+                      const Epi& epi, bool* launched) {
+  *launched = false;
+  int n_tiles, BN;
+  tma_n_tiles(N, &n_tiles, &BN);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, K, lda, tmag::kBM) || !make_map(&mb, B, N, K, ldb, BN)) return RMC_OK;
+  tmag::Args g{M, N, K, BN, (M + tmag::kBM - 1) / tmag::kBM, n_tiles, ctx->d_status + 3};
+  const int tiles = g.m_tiles * g.n_tiles;
+  const int grid = std::min(tiles, sm_count());
+  // the attribute is process-wide: always the largest size any launch needs
+  if (tmag::stages_for(BN) == 3) {
+    CK(cudaFuncSetAttribute(tmag::gemm_tma_tf32x3_kernel<3, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)tmag::smem_bytes(128, 3)));
+    tmag::gemm_tma_tf32x3_kernel<3, Epi><<<grid, tmag::kThreads, tmag::smem_bytes(BN, 3), ctx->stream>>>(ma, mb, g, epi);
+  } else {
+    CK(cudaFuncSetAttribute(tmag::gemm_tma_tf32x3_kernel<2, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)tmag::smem_bytes(256, 2)));
+    tmag::gemm_tma_tf32x3_kernel<2, Epi><<<grid, tmag::kThreads, tmag::smem_bytes(BN, 2), ctx->stream>>>(ma, mb, g, epi);
+  }
+  CKL();
+  *launched = true;
+  return RMC_OK;
+}
+
 rmc_status kron_apply_tc(rmc_ctx* ctx, const KronOp<float>& H, const float* X, int nv, float* Y, float alpha,
                          float beta, float gamma, const float* Z, float* Tbuf) {
   const int kA = H.kA, kB = H.kB, no = H.n_ops;
   ProfScope ps(ctx, 0, (double)nv * ((double)2 * no * kA * kB * (kA + kB) + 3.0 * kA * kB));
-  TRY(launch_tc(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, EpiKron1T<float>{Tbuf, kA, kB, no}));
-  TRY(launch_tc(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA,
-                EpiKron2T<float>{X, Z, H.EA, H.EB, Y, kA, kB, alpha, beta, gamma}));
+  // stage 1: T'[(v, b)][(j, a)] = sum_b' X[v][a][b'] B_j[b][b']; stage 2:
+  // Y^T rows (v, b) = T' Acat^T.  Each stage on the TMA-fed kernel when the
+  // TMA can address its operands, else on the plain-load kernel.
+  bool done = false;
+  const EpiKron1T<float> e1{Tbuf, kA, kB, no};
+  TRY(launch_tma(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, e1, &done));
+  if (!done) TRY(launch_tc(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, e1));
+  const EpiKron2T<float> e2{X, Z, H.EA, H.EB, Y, kA, kB, alpha, beta, gamma};
+  TRY(launch_tma(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA, e2, &done));
+  if (!done) TRY(launch_tc(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA, e2));
   return RMC_OK;
 }
 

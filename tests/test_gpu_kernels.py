@@ -30,6 +30,52 @@ def ctx():
     c.close()
 
 
+def tc_shape_ok(kA, kB, n_ops):
+    """Stage 1 (contraction over kB, N = n_ops*kB) runs on the TMA-fed kernel
+    when kB is a multiple of 4 (16-byte row pitch), else on the plain-load one
+    (N <= 256); stage 2 (contraction over n_ops*kA, N = kA) likewise."""
+    s1 = kB % 4 == 0 or n_ops * kB <= 256
+    s2 = (n_ops * kA) % 4 == 0 or kA <= 256
+    return n_ops >= 1 and s1 and s2
+
+
+def _kron_reference(EA, EB, oA, oB, coef, X, alpha, beta, gamma, Z):
+    """Eq. (7) applied in Kronecker form, FP64: Y_v = D o X_v + sum_j c_j A_j X_v B_j^T,
+    then alpha Y + beta X + gamma Z (for shapes whose dense H_eff is too large)."""
+    Y = (EA[:, None] + EB[None, :])[None] * X
+    for j in range(len(coef)):
+        Y = Y + coef[j] * np.einsum("ab,vbc,dc->vad", oA[j], X, oB[j], optimize=True)
+    return alpha * Y + beta * X + gamma * Z
+
+
+WIDE_SHAPES = [(256, 256, 3, 5), (200, 256, 3, 7), (256, 192, 2, 9), (128, 128, 3, 40), (96, 250, 3, 3)]
+
+
+@pytest.mark.parametrize("kA,kB,n_ops,nv", WIDE_SHAPES)
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_wide_kron_matvec_matches_kronecker_form(ctx, kA, kB, n_ops, nv, dtype):
+    """The shapes of the 256-state merges (stage-1 N = n_ops*kB up to 768, split
+    into N tiles; ragged kA = 200 -> a 208-column tile; kB = 250 is not a
+    multiple of 4, so stage 1 falls back or is refused) against Eq. (7) in
+    Kronecker form in FP64."""
+    if dtype == 2 and not tc_shape_ok(kA, kB, n_ops):
+        pytest.skip("outside the tensor-core kernels' shapes")
+    rng = np.random.default_rng(kA * 3 + kB * 5 + n_ops + 11 * dtype)
+    EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
+    X = rng.standard_normal((nv, kA, kB))
+    Z = rng.standard_normal((nv, kA, kB))
+    for alpha, beta, gamma in [(1.0, 0.0, 0.0), (0.21, 0.5, -0.8)]:
+        ref = _kron_reference(EA, EB, oA, oB, coef, X, alpha, beta, gamma, Z)
+        d = [dev(a, np.float32) for a in (EA, EB, oA, oB, X, Z)]
+        Y = dev(np.full_like(X, np.nan), np.float32)
+        torch_cuda().cuda.synchronize()
+        ctx.kron_matvec(dtype, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(),
+                        d[3].data_ptr(), coef, d[4].data_ptr(), Y.data_ptr(), d[5].data_ptr(), alpha, beta, gamma)
+        got = host(Y)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(got - ref).max() <= 3e-5 * scale, (alpha, beta, gamma, np.abs(got - ref).max() / scale)
+
+
 def _dense_reference(EA, EB, oA, oB, coef, X, alpha, beta, gamma, Z):
     H = O.effective_hamiltonian(EA, EB, [(coef[j], oA[j], oB[j]) for j in range(len(coef))])
     nv, kA, kB = X.shape
@@ -44,9 +90,10 @@ def _dense_reference(EA, EB, oA, oB, coef, X, alpha, beta, gamma, Z):
 @pytest.mark.parametrize("dtype", [0, 1, 2])
 def test_kron_matvec_matches_dense_heff(ctx, kA, kB, n_ops, nv, dtype):
     """dtype 0: FP64; 1: FP32 on the FP32 pipe; 2: FP32 data on the tcgen05
-    tensor cores (3xTF32), defined for n_ops >= 1, n_ops*kB <= 256, kA <= 256."""
-    if dtype == 2 and not (n_ops >= 1 and n_ops * kB <= 256 and kA <= 256):
-        pytest.skip("outside the tensor-core kernel's shapes")
+    tensor cores (3xTF32), defined where each stage fits one of the two
+    tensor-core kernels (tc_shape_ok)."""
+    if dtype == 2 and not tc_shape_ok(kA, kB, n_ops):
+        pytest.skip("outside the tensor-core kernels' shapes")
     rng = np.random.default_rng(kA * 1000 + kB * 10 + n_ops + dtype)
     EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
     X = rng.standard_normal((nv, kA, kB))
