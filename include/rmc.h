@@ -56,13 +56,17 @@ typedef enum rmc_precision {
   RMC_PREC_FP64 = 0,
   /* Filter, orthogonalisation and Rayleigh-Ritz of the subspace iteration in
    * FP32 (FP32 accumulation); every merge then refines the converged block
-   * with one FP64 Chebyshev filter pass and ends with the FP64 finalisation
-   * (FP64 Cholesky-QR, FP64 Rayleigh-Ritz with refined eigenvectors, FP64
-   * rotation), so energies and retained bases are FP64-consistent
-   * projections. */
+   * to an FP64 residual of 1e-8 (Chebyshev filter passes; for blocks wider
+   * than the small eigensolver in defect form, FP32 products on the small
+   * correction) and ends with the FP64 finalisation (FP64 Cholesky-QR, FP64
+   * Rayleigh-Ritz with refined eigenvectors, FP64 rotation), so energies and
+   * retained bases are FP64-consistent projections.  The Kronecker products
+   * of wide merges (k_A k_B >= 16384, row pitches of 16 bytes) run on the
+   * tcgen05 tensor cores in 3xTF32 (FP32 accuracy), the rest on the FP32
+   * pipe. */
   RMC_PREC_MIXED = 1,
-  /* As RMC_PREC_MIXED with the Kronecker products of the filter on the tcgen05
-   * tensor cores (TF32 operands, FP32 accumulation). */
+  /* As RMC_PREC_MIXED with every Kronecker product of the working precision
+   * that fits a tensor-core kernel on the tcgen05 tensor cores (3xTF32). */
   RMC_PREC_MIXED_TF32 = 2
 } rmc_precision;
 

@@ -630,12 +630,24 @@ rmc_status kron_apply_tc(rmc_ctx* ctx, const KronOp<float>& H, const float* X, i
 
 // The working-precision product of the subspace iteration: tensor cores for
 // the TF32 mixed path when the shape fits, SIMT otherwise.
+// RMC_PREC_MIXED_TF32 takes the tensor cores wherever a stage fits; the
+// default mixed path takes them for wide merges whose both stages the TMA-fed
+// kernel can address (k_A k_B >= 16384 and 16-byte row pitches), where they
+// are 2-4x faster than the FP32 pipe (measured at k = 128 and 256); smaller
+// products stay on the FP32 pipe, where the tensor-core form is not faster.
+bool tc_wide(int kA, int kB, int n_ops) {
+  return n_ops > 0 && (long)kA * kB >= 16384 && tma_fits(kB, kB, kB) &&
+         tma_fits((long)n_ops * kA, (long)n_ops * kA, n_ops * kA);
+}
+
 template <typename T>
 rmc_status kron_work(rmc_ctx* ctx, const KronOp<T>& H, const T* X, int nv, T* Y, T alpha, T beta, T gamma,
                      const T* Z, T* Tbuf) {
   if constexpr (sizeof(T) == 4) {
-    if (ctx->cfg.precision == RMC_PREC_MIXED_TF32 && tc_fits(H.kA, H.kB, H.n_ops))
-      return kron_apply_tc(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
+    const bool tc = ctx->cfg.precision == RMC_PREC_MIXED_TF32 ? tc_fits(H.kA, H.kB, H.n_ops)
+                    : ctx->cfg.precision == RMC_PREC_MIXED  ? tc_wide(H.kA, H.kB, H.n_ops)
+                                                             : false;
+    if (tc) return kron_apply_tc(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
   }
   return kron_apply<T>(ctx, H, X, nv, Y, alpha, beta, gamma, Z, Tbuf);
 }
@@ -1071,19 +1083,43 @@ rmc_status project_out(rmc_ctx* ctx, const W* Xl, int nl, W* Xa, int na, long n,
 // rounding-level locked components of X would grow by T_deg at the locked
 // eigenvalues, far faster than the wanted ones, and swamp them in working
 // precision.
+//
+// The locked span need not be removed after every product: a rounding-level
+// locked component grows, relative to the scaled wanted ones, by the scalar
+// recurrence evaluated at the lowest locked eigenvalue theta_lock (which has
+// the fastest growth below the damped interval).  With theta_lock given, a
+// term is deflated once that growth since the last deflation exceeds
+// kDeflateGrowth, and the last term is left to the caller's orthonormalisation
+// (which removes the locked span twice); with theta_lock NaN every term is
+// deflated.
+constexpr double kDeflateGrowth = 10.0;
+
 template <typename W>
 rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX, int b, double theta0, double a,
                        double ub, int deg, W* Y0, W* Y1, W* Y2, W* Tbuf, W** out, const W* Ql = nullptr,
-                       int nl = 0, W* Cbuf = nullptr) {
+                       int nl = 0, W* Cbuf = nullptr, double theta_lock = NAN) {
   const long n = H.n();
   const double e = (ub - a) / 2, c = (ub + a) / 2;
   double sigma = e / (theta0 - c);
   const double tau = 2.0 / sigma;
+  const bool every = std::isnan(theta_lock);
+  // the scalar recurrence at theta_lock, and its value at the last deflation
+  double yl_prev = 1.0, yl = sigma / e * (theta_lock - c), yl_ref = 1.0;
+  auto due = [&](int d, double y) {
+    if (nl <= 0) return false;
+    if (every) return true;
+    if (d == deg) return false;
+    if (std::fabs(y) > kDeflateGrowth * std::fabs(yl_ref)) {
+      yl_ref = y;
+      return true;
+    }
+    return false;
+  };
   // Y1 = (sigma/e) (H X - c X), from the stored H X
   axpby_kernel<W><<<grid1d((long)b * n), 256, 0, ctx->stream>>>(HX, X, (long)b * n, W(sigma / e),
                                                                  W(-c * sigma / e), Y1);
   CKL();
-  TRY(project_out<W>(ctx, Ql, nl, Y1, b, n, Cbuf, 1));
+  if (due(1, yl)) TRY(project_out<W>(ctx, Ql, nl, Y1, b, n, Cbuf, 1));
   const W* Yprev = X;
   W* Ycur = Y1;
   W* Ynext = Y2;
@@ -1091,7 +1127,10 @@ rmc_status cheb_filter(rmc_ctx* ctx, const KronOp<W>& H, const W* X, const W* HX
   for (int d = 2; d <= deg; ++d) {
     const double s1 = 1.0 / (tau - sigma);
     TRY(kron_work<W>(ctx, H, Ycur, b, Ynext, W(2 * s1 / e), W(-2 * s1 * c / e), W(-sigma * s1), Yprev, Tbuf));
-    TRY(project_out<W>(ctx, Ql, nl, Ynext, b, n, Cbuf, 1));
+    const double yl_next = 2 * s1 / e * (theta_lock - c) * yl - sigma * s1 * yl_prev;
+    yl_prev = yl;
+    yl = yl_next;
+    if (due(d, yl)) TRY(project_out<W>(ctx, Ql, nl, Ynext, b, n, Cbuf, 1));
     // rotate: the buffer two steps back is free unless it is X itself
     W* old_prev = const_cast<W*>(Yprev);
     Yprev = Ycur;
@@ -1291,6 +1330,7 @@ rmc_status chfsi_locked(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b_t
   CKL();
   *converged = true;
   int total_it = 0;
+  double theta_lock = NAN;  // lowest locked Ritz value (the first chunk's first)
   for (int L = 0; L < k_conv;) {
     const int c = std::min(chunk, k_conv - L);
     const int ba = std::min(b_total - L, c + kGuard);
@@ -1351,12 +1391,14 @@ rmc_status chfsi_locked(rmc_ctx* ctx, Workspace& ws, const KronOp<W>& H, int b_t
       int deg = (int)std::floor(std::acosh(rho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
       deg = std::max(2, std::min(dmax, deg));
       W* Yout = nullptr;
-      TRY((cheb_filter<W>(ctx, H, Xa, HXa, ba, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout, X, L, C)));
+      TRY((cheb_filter<W>(ctx, H, Xa, HXa, ba, th[0], a, ub, deg, Y0, Y1, Y2, Tbuf, &Yout, X, L, C,
+                          L > 0 ? theta_lock : NAN)));
       CK(cudaMemcpyAsync(Xa, Yout, sizeof(W) * ba * n, cudaMemcpyDeviceToDevice, ctx->stream));
       TRY(orthonormalise());
       TRY(rayleigh_ritz());
     }
     if (!*converged) break;
+    if (L == 0) theta_lock = th[0];
     L += c;
   }
   *iters_out = total_it;
