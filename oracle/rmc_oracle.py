@@ -300,7 +300,10 @@ def lowest_eigenpairs(H: np.ndarray, count: int, full_max: Optional[int] = None)
     if n <= lim or count >= n:
         return np.linalg.eigh(H)
     import scipy.linalg as sl
-    return sl.eigh(H, subset_by_index=[0, count - 1], driver="evr", overwrite_a=True, check_finite=False)
+    # H is symmetric, so its transpose view is the same matrix; that view is
+    # Fortran-ordered, which LAPACK takes without a copy (a 65536-row matrix is
+    # 34 GB)
+    return sl.eigh(H.T, subset_by_index=[0, count - 1], driver="evr", overwrite_a=True, check_finite=False)
 
 
 def rotate_operator(C: np.ndarray, o: np.ndarray, side: int, kA: int, kB: int) -> np.ndarray:
