@@ -1,26 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the recursive module-coupling eigensolver on B300.
 
-Workload (one step): the XXZ Heisenberg chain N = 32, Delta = 1, bond couplings
-J_i ~ U[0.5, 1.5] (seeded), leaves of 4 spins, k = 64 retained states per
-level (effective dimension 4096, three boundary operators per bond), depth 3,
-the 8 lowest states -- solved for a batch of independent instances, each
-through the whole hot path (leaf build, every merge: diagonal and start block,
-Chebyshev-filtered subspace iteration on the Kronecker-form product, FP64
-finalisation, cut, gauge, operator rotation).
+Default workload (one step): one solve of the random-field Heisenberg chain
+N = 128, Delta = 1, J = 1, on-site fields h_i ~ U[-2, 2] (seeded), leaves of 4
+spins, k = 256 retained states per level (merges of effective dimension 65536,
+three boundary operators per bond), the 16 lowest states -- the largest
+single-GPU configuration of the benchmark set -- through the whole hot path
+(leaf build, every merge: diagonal and start block, Chebyshev-filtered
+subspace iteration on the Kronecker-form product, FP64 refinement and
+finalisation, cut, gauge, operator rotation), by the public C-ABI call
+rmc_solve_chain (host arrays in, host energies out).
 
-Metric: solves/s at 1e-8 relative energy error (a solve counts only if every
-energy is within 1e-8 * max(1, |E|) of the oracle's stored value), with p50 /
-p99 per-solve latency and the Kronecker-matvec throughput beside it.
+Metric: solves/s at 1e-8 relative energy error.  A solve counts only if every
+energy is within 1e-8 * max(1, |E|) of the reference, which for this size is
+the plain FP64 GPU path on the same instance (the CPU oracle cannot form the
+65536-dimensional merges in bounded time; it is checked at k = 128 on the same
+chain in the tests).  That FP64 solve is also the "plain FP64 per-solve" arm.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision mixed|fp64] [--batch B]
+                    [--workload rfheis|xxz|serving] [--precision mixed|fp64|mixed_tf32]
 
-A step submits the batch to a solve server with ``--slots`` concurrent slots
-(worker threads with their own CUDA streams) and waits for every result.
-Under torchrun every rank solves its own batch of independent instances
-(replicas: the solves shard with no exchange), timing is the max over ranks.
-``--impl reference`` times the CPU oracle (the reference arm: there is no reference implementation).
+--workload xxz: the batched XXZ N = 32, k = 64 benchmark (32 instances per step
+through the solve server, oracle-validated); --workload serving: Poisson
+request stream of mixed chains through the continuous-batching server.
+Under torchrun every rank solves its own instances (replicas: the solves shard
+with no exchange); timing is the max over ranks.  ``--impl reference`` times
+the CPU oracle (the reference arm: there is no reference implementation).
 """
 from __future__ import annotations
 
@@ -37,27 +42,33 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# The solve server runs one CUDA stream per slot; the driver maps streams onto
-# CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless set), and kernels of
-# streams that share a queue run in order, so with 16 slots a long one-CTA
-# kernel of one solve holds back another's.  It must be set before the CUDA
-# context exists (measured on one B300: 40.1 -> 73.5 solves/s with 32).
+# Concurrent solves and merge lanes each run on their own CUDA stream; the
+# driver maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless
+# set), and kernels of streams that share a queue run in order.  It must be set
+# before the CUDA context exists.
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
 import instances as I  # noqa: E402
 
-GOLD = os.path.join(ROOT, "tests", "golden", "bench_xxz_n32_k64.json")
-METRIC = "solves/s at 1e-8 energy error (XXZ N=32, k=64, 8 lowest states)"
-UNIT = "solves/s"
 RTOL = 1e-8
-WORKLOAD = "xxz_n32_k64"
+UNIT = "solves/s"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB of L2
+GOLD_XXZ = os.path.join(ROOT, "tests", "golden", "bench_xxz_n32_k64.json")
+GOLD_K128 = os.path.join(ROOT, "tests", "golden", "rfheis_n128_k128.json")
+
+WORKLOADS = {
+    "rfheis": {"name": "rfheis_n128_k256", "metric": "solves/s at 1e-8 energy error (random-field Heisenberg "
+                                                       "N=128, k=256, 16 lowest states)"},
+    "xxz": {"name": "xxz_n32_k64", "metric": "solves/s at 1e-8 energy error (XXZ N=32, k=64, 8 lowest states)"},
+}
 
 # Peak FP32 FMA throughput of the SIMT pipe: 148 SMs x 128 lanes x 2 FLOP x
 # 2.032 GHz (unit counts and maximum clock of the part).
 FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+TF32_PER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rates of the part
+FP64_PIPE_TFLOPS = 1.13         # DFMA throughput loop measured on this part
 
 
 def parse_args():
@@ -66,35 +77,45 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rfheis", choices=["rfheis", "xxz", "serving"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_tf32"])
-    ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=0, help="instances per step (rfheis: 1, xxz: 32)")
+    ap.add_argument("--slots", type=int, default=16, help="xxz / serving: solve-server slots")
+    ap.add_argument("--lanes", type=int, default=0, help="rfheis: merge lanes (0: the library default, 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="rfheis: skip the XXZ batch and kernel-alone timings")
     ap.add_argument("--no-autotune", action="store_true", help="skip the tile-tuning solve before warm-up")
-    ap.add_argument("--profile-all-kinds", action="store_true",
-                    help="time every kernel kind during the timed region (more host-side event records)")
-    ap.add_argument("--workload", default="xxz", choices=["xxz", "serving"],
-                    help="xxz: the batched XXZ N=32 k=64 benchmark (default); serving: Poisson request "
-                         "stream of mixed chains through the continuous-batching server")
-    ap.add_argument("--rates", default="10,100,1000", help="serving: arrival rates in requests/s")
+    ap.add_argument("--rates", default="10,30,100,300,1000", help="serving: arrival rates in requests/s")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests per rate")
-    ap.add_argument("--check", type=int, default=6, help="serving: requests re-solved alone in FP64 to check")
     return ap.parse_args()
 
 
-def load_gold():
-    with open(GOLD) as f:
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"bf16": d["bf16_tflops"], "bf16_sustained": d.get("bf16_tflops_sustained"), "hbm": d["hbm_gbs"],
+                "source": "measured (MEASURED_PEAKS.json)"}
+    return {"bf16": 1800.0, "bf16_sustained": 1400.0, "hbm": 6400.0, "source": "fallback"}
+
+
+def rf_seeds(rank: int, batch: int):
+    """Rank r solves instances r*batch .. r*batch+batch-1; instance 0 is the
+    benchmark's own seed (2609*100 + 4)."""
+    return [I.seed_for(4) + 7919 * i for i in range(rank * batch, (rank + 1) * batch)]
+
+
+def load_gold_xxz():
+    with open(GOLD_XXZ) as f:
         return {d["seed"]: np.array(d["energies"]) for d in json.load(f)["instances"]}
 
 
-def batch_seeds(rank: int, batch: int, gold_seeds):
-    """Rank r solves instances r*batch .. r*batch+batch-1 of the seed sequence
-    (the first ones are those with stored oracle energies)."""
+def xxz_seeds(rank: int, batch: int, gold_seeds):
+    """Every rank solves instances with stored oracle energies: rank r takes
+    the stored seeds from position r*batch on, wrapping around the stored set
+    (independent replicas may repeat instances)."""
     base = sorted(gold_seeds)
-    out = []
-    for i in range(rank * batch, (rank + 1) * batch):
-        out.append(base[i] if i < len(base) else I.seed_for(2) + 7919 * i)
-    return out
+    return [base[i % len(base)] for i in range(rank * batch, (rank + 1) * batch)]
 
 
 class ClockSampler:
@@ -159,21 +180,12 @@ def dist_setup():
     return world, rank, local, pg
 
 
-def reduce_max(pg, value: float, device) -> float:
+def reduce_op(pg, value: float, device, op: str) -> float:
     if pg is None:
         return value
     import torch
     t = torch.tensor([value], dtype=torch.float64, device=device)
-    pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    return float(t.item())
-
-
-def reduce_sum(pg, value: float, device) -> float:
-    if pg is None:
-        return value
-    import torch
-    t = torch.tensor([value], dtype=torch.float64, device=device)
-    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX if op == "max" else pg.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -182,11 +194,20 @@ def chain_bytes(chain) -> int:
     return len(chain.onsite) * (4 + 1 + 8) + len(chain.bonds) * (4 + 4 + 1 + 1 + 8)
 
 
+def within(E, ref) -> bool:
+    return ref is not None and bool(np.all(np.abs(np.asarray(E) - ref) <= RTOL * np.maximum(1.0, np.abs(ref))))
+
+
+def percentile(vals, p):
+    v = sorted(vals)
+    return v[min(len(v) - 1, int(round(p * (len(v) - 1))))]
+
+
 # ---------------------------------------------------------------------------
 # CPU legs: the oracle (allowed here only)
 # ---------------------------------------------------------------------------
 
-def _oracle_threads() -> int:
+def _blas_threads() -> int:
     try:
         from threadpoolctl import threadpool_info
         return max([d.get("num_threads", 1) for d in threadpool_info() if d.get("user_api") == "blas"] or [1])
@@ -194,102 +215,146 @@ def _oracle_threads() -> int:
         return len(os.sched_getaffinity(0))
 
 
-def oracle_merge_sample(chain, position: int):
-    """Time the oracle on one merge (by post-order position) of the chain's
-    recursion, leaves included for that merge: a bounded sample of one solve."""
+def _merge_nodes(chain):
     from oracle import rmc_oracle as O
     tree = O.split_tree(0, chain.n_sites, chain.leaf_sites)
-    merges = []
+    out = []
 
-    def collect(node, top):
+    def walk(node, top, depth):
         if isinstance(node[0], int):
             return
-        collect(node[0], False)
-        collect(node[1], False)
-        merges.append((node, top))
-    collect(tree, True)
-    node, top = merges[position % len(merges)]
-    # inputs of this merge: the two child blocks (built untimed)
+        walk(node[0], False, depth + 1)
+        walk(node[1], False, depth + 1)
+        out.append((node, top, depth))
+    walk(tree, True, 0)
+    return out
 
-    def build(nd, is_top):
-        if isinstance(nd[0], int):
-            return O.leaf_block(chain, nd[0], nd[1], chain.k, is_top)
-        A = build(nd[0], False)
-        B = build(nd[1], False)
-        return O.merge_blocks(chain, A, B, chain.k, is_top)[0]
-    A = build(node[0], False)
-    B = build(node[1], False)
+
+def _oracle_block(chain, node, top):
+    from oracle import rmc_oracle as O
+    if isinstance(node[0], int):
+        return O.leaf_block(chain, node[0], node[1], chain.k, top)
+    A = _oracle_block(chain, node[0], False)
+    B = _oracle_block(chain, node[1], False)
+    return O.merge_blocks(chain, A, B, chain.k, top)[0]
+
+
+def oracle_merge_time(chain, node, top) -> float:
+    """The oracle's time for one merge (its two input blocks built untimed)."""
+    from oracle import rmc_oracle as O
+    A = _oracle_block(chain, node[0], False)
+    B = _oracle_block(chain, node[1], False)
     t0 = time.perf_counter()
     O.merge_blocks(chain, A, B, chain.k, top)
-    return time.perf_counter() - t0, len(merges)
+    return time.perf_counter() - t0
 
 
-def oracle_solve_time_estimate(chain, budget_s: float):
-    """Estimate the oracle's time per solve from per-merge samples (each merge
-    timed once, leaves timed once), stopping early when the budget runs out."""
+def oracle_rfheis_estimate(rep: int = 0):
+    """The oracle's time for one solve of the k = 256 random-field chain,
+    from a bounded sample: the 32 leaves and the 16 level-1 merges (dimension
+    256, exact) are timed whole; the 15 merges of dimension 65536 (one dense
+    65536 x 65536 H_eff each, 34 GB) are extrapolated from one timed merge of
+    dimension 16384 of the same chain at k = 128 (a level-2 merge, position
+    `rep`) by (65536/16384)^3 = 64, the Theta(k^6) = Theta(n^3) per-merge cost
+    of the dense eigensolve (Appendix A)."""
     from oracle import rmc_oracle as O
+    ch = I.rf_heisenberg_n128(k=256)
     t0 = time.perf_counter()
-    tree = O.split_tree(0, chain.n_sites, chain.leaf_sites)
     leaves = []
 
     def lv(nd):
         if isinstance(nd[0], int):
             leaves.append(nd)
         else:
-            lv(nd[0]); lv(nd[1])
-    lv(tree)
+            lv(nd[0])
+            lv(nd[1])
+    lv(O.split_tree(0, ch.n_sites, ch.leaf_sites))
     for nd in leaves:
-        O.leaf_block(chain, nd[0], nd[1], chain.k)
-    leaf_t = time.perf_counter() - t0
-    total = leaf_t
-    _, n_m = oracle_merge_sample(chain, 0)
-    sampled = 0
-    for pos in range(n_m):
-        dt, _ = oracle_merge_sample(chain, pos)
-        total += dt
-        sampled += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    if sampled < n_m:
-        total = leaf_t + (total - leaf_t) * n_m / sampled
-    return total, sampled, n_m
+        O.leaf_block(ch, nd[0], nd[1], ch.k)
+    t_leaves = time.perf_counter() - t0
+    merges = _merge_nodes(ch)
+    deepest = max(d for _, _, d in merges)
+    t_l1 = sum(oracle_merge_time(ch, nd, top) for nd, top, d in merges if d == deepest)
+    c128 = I.rf_heisenberg_n128(k=128)
+    lvl2 = [(nd, top) for nd, top, d in _merge_nodes(c128) if d == deepest - 1]
+    nd, top = lvl2[rep % len(lvl2)]
+    t16k = oracle_merge_time(c128, nd, top)
+    n_big = sum(1 for _, _, d in merges if d < deepest)
+    est = t_leaves + t_l1 + n_big * 64.0 * t16k
+    sample = (f"leaves + {sum(1 for *_, d in merges if d == deepest)} level-1 merges (n=256) timed; "
+              f"{n_big} merges of n=65536 extrapolated x64 from one timed n=16384 merge ({t16k:.1f} s, k=128 "
+              f"level-2 merge #{rep % len(lvl2)}): Theta(n^3) dense eigensolve")
+    return est, sample, time.perf_counter() - t0
+
+
+def oracle_xxz_solve_time(chain):
+    """Whole oracle solve of one XXZ N=32 instance."""
+    from oracle import rmc_oracle as O
+    t0 = time.perf_counter()
+    E = O.solve(chain).energies
+    return time.perf_counter() - t0, E
+
+
+def oracle_xxz_one_thread() -> float:
+    """The same solve with one BLAS / OpenMP thread (the paper's CPU setting),
+    in a child process started with the thread counts fixed in its
+    environment (they must be set before the BLAS library loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, time; sys.path.insert(0, %r); import instances as I; from oracle import rmc_oracle as O; "
+            "c = I.xxz_n32(); t0 = time.perf_counter(); O.solve(c); print(time.perf_counter() - t0)" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    return float(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
     """The reference arm: the oracle as it stands (NumPy + LAPACK, dense eigh of
-    every H_eff, Algorithm 1 as written) on the host cores.  A step is one whole
-    oracle solve of one of the same seeded instances the GPU arm solves (about
-    7 s on 16 host cores), so value is measured, not extrapolated."""
-    from oracle import rmc_oracle as O
-    # rank 0 alone runs it; the others exit without work (no process group:
-    # the oracle needs no collective and no GPU)
+    every H_eff, Algorithm 1 as written) on the host cores, rank 0 only (no
+    process group: the oracle needs no collective and no GPU).  rfheis: each
+    step is the bounded sample of oracle_rfheis_estimate (extrapolated solve
+    time); xxz: each step is one whole oracle solve, checked against the
+    stored energies."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    gold = load_gold()
-    seeds = batch_seeds(0, args.batch, gold.keys())
-    chains = [I.xxz_n32(sd) for sd in seeds]
-    for s in range(args.warmup):
-        O.solve(chains[s % len(chains)])
-    times, valid = [], 0
-    for s in range(args.steps):
-        sd = seeds[s % len(seeds)]
-        t0 = time.perf_counter()
-        E = O.solve(chains[s % len(chains)]).energies
-        times.append(time.perf_counter() - t0)
-        ref = gold.get(sd)
-        valid += int(ref is not None and np.all(np.abs(E - ref) <= RTOL * np.maximum(1.0, np.abs(ref))))
-    value = valid / sum(times)
-    cores = _oracle_threads()
+    wl = WORKLOADS["xxz" if args.workload == "xxz" else "rfheis"]
+    cores = _blas_threads()
+    times = []
+    if args.workload == "xxz":
+        gold = load_gold_xxz()
+        seeds = xxz_seeds(0, max(args.steps, 1), gold.keys())
+        for s in range(args.warmup):
+            oracle_xxz_solve_time(I.xxz_n32(seeds[s % len(seeds)]))
+        valid = 0
+        for s in range(args.steps):
+            dt, E = oracle_xxz_solve_time(I.xxz_n32(seeds[s]))
+            times.append(dt)
+            valid += int(within(E, gold.get(seeds[s])))
+        value = valid / sum(times)
+        sample = f"{args.steps} whole oracle solves (seeds {seeds[0]}...), one a step"
+        config = {"workload": wl["name"], "N": 32, "k": 64, "q": 8, "L0": 4, "delta": 1.0}
+    else:
+        from oracle import rmc_oracle as O
+        for s in range(args.warmup):          # warm-up: the leaves only (imports, BLAS start-up)
+            ch = I.rf_heisenberg_n128(k=256)
+            O.leaf_block(ch, 0, 4, ch.k)
+        samples, took = [], []
+        for s in range(args.steps):
+            est, sample, dt = oracle_rfheis_estimate(s)
+            times.append(est)
+            samples.append(sample)
+            took.append(dt)
+        value = 1.0 / statistics.mean(times)
+        valid = args.steps
+        sample = ("per step: " + samples[0] + "; value = 1 / mean extrapolated solve time "
+                  f"({statistics.mean(times):.0f} s a solve)")
+        times = took                           # ms_per_step: the host time each sample took
+        config = {"workload": wl["name"], "N": 128, "k": 256, "q": 16, "L0": 4, "delta": 1.0, "fields": "U[-2,2]"}
+    config.update({"precision": "fp64 dense eigh (oracle)", "l2": "n/a (CPU)"})
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded XXZ chains, J_i ~ U[0.5,1.5])",
-        "config": {"workload": WORKLOAD, "N": 32, "k": 64, "q": 8, "L0": 4, "delta": 1.0,
-                   "precision": "fp64 dense eigh (oracle)", "l2": "n/a (CPU)"},
-        "valid_solves": valid, "solves": args.steps,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} whole oracle solves (seeds {seeds[0]}...), one a step"},
+        "data": "synthetic (seeded spin chains)", "config": config, "valid_solves": valid, "solves": args.steps,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -299,51 +364,100 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_alone(P, torch, dev, reps: int = 20):
-    """The fused Chebyshev filter alone (after the timed region) on the
-    workload's dominant merge shape: 96 vectors of 64 x 64, three coupling
-    operators, degree 10; CUDA events on the context's stream around `reps`
-    launches.  FP32 on the FP32 pipe (the subspace iteration's filter) and FP64
-    data in double-FP32 arithmetic (the refinement's filter).  Algorithmic
-    FLOPs: 2 n_ops kA kB (kA + kB) + 3 kA kB per vector and product."""
-    kA = kB = 64
-    n_ops, nv, deg = 3, 96, 10
-    rng = np.random.default_rng(7)
-    EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, n_ops)
-    X = rng.standard_normal((nv, kA, kB))
-    flops = nv * deg * (2.0 * n_ops * kA * kB * (kA + kB) + 3.0 * kA * kB)
+def time_launches(torch, stream, launch, reps: int = 10) -> float:
+    for _ in range(3):
+        launch()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        launch()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def kernel_alone(P, torch, dev, pk):
+    """The Kronecker-form product alone, on the context's stream with CUDA
+    events, on the dominant shapes of the k = 256 merges: kA = kB = 256, three
+    operators, 160 vectors (the active block of the locked subspace
+    iteration) and 288 (the refinement's block); tcgen05 3xTF32 (the default
+    mixed path's product at this size) and the FP32 SIMT form.  Algorithmic
+    FLOPs: 2 n_ops kA kB (kA + kB) + 3 kA kB per vector.  Plus the fused FP32
+    Chebyshev filter on the XXZ k = 64 shape (96 vectors of 64 x 64, three
+    operators, degree 10)."""
     out = {}
+    tf32_peak = pk["bf16"] * TF32_PER_BF16
+    with P.Context(precision="fp64", device=dev.index) as ctx:
+        stream = torch.cuda.ExternalStream(ctx.stream)
+        for nv in (160, 288):
+            kA = kB = 256
+            no = 3
+            rng = np.random.default_rng(7)
+            EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, no)
+            d = [torch.tensor(a, dtype=torch.float32, device=dev) for a in (EA, EB, oA, oB,
+                                                                           rng.standard_normal((nv, kA, kB)))]
+            Y = torch.empty_like(d[4])
+            flops = nv * (2.0 * no * kA * kB * (kA + kB) + 3.0 * kA * kB)
+            for dt, name in ((2, "tcgen05_3xtf32"), (1, "fp32_simt")):
+                ms = time_launches(torch, stream, lambda: ctx.kron_matvec(
+                    dt, kA, kB, no, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(), coef,
+                    d[4].data_ptr(), Y.data_ptr()))
+                tf = flops / (ms / 1e3) / 1e12
+                rec = {"ms": ms, "algorithmic_tflops": tf, "launches": 2}
+                if dt == 2:
+                    rec.update({"tf32_peak_tflops": tf32_peak, "frac_of_tf32_peak": tf / tf32_peak,
+                                "mma_frac_of_tf32_peak": 3 * tf / tf32_peak})
+                else:
+                    rec.update({"fp32_pipe_peak_tflops": FP32_SIMT_PEAK_TFLOPS,
+                                "frac_of_fp32_pipe": tf / FP32_SIMT_PEAK_TFLOPS})
+                out[f"kron_256x256x3_nv{nv}_{name}"] = rec
     with P.Context(precision="mixed", device=dev.index) as ctx:
         stream = torch.cuda.ExternalStream(ctx.stream)
-        for name, dtype, tdt in (("fused_filter_fp32", 1, torch.float32), ("fused_filter_df64", 3, torch.float64)):
-            d = [torch.tensor(a, dtype=tdt, device=dev) for a in (EA, EB, oA, oB, X)]
-            Y = torch.empty_like(d[4])
-            torch.cuda.synchronize()
-
-            def launch():
-                ctx.cheb_filter(dtype, kA, kB, n_ops, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(),
-                                d[3].data_ptr(), coef, d[4].data_ptr(), deg, -20.0, -10.0, 10.0, True, Y.data_ptr())
-            for _ in range(3):
-                launch()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                launch()
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            tf = flops / (ms / 1e3) / 1e12
-            if dtype == 1:
-                out[name] = {"ms": ms, "achieved_tflops": tf, "peak_tflops": FP32_SIMT_PEAK_TFLOPS,
-                             "frac": tf / FP32_SIMT_PEAK_TFLOPS, "bound": "alu", "ctas": nv,
-                             "peak_source": "FP32 FMA pipe: 148 SMs x 128 lanes x 2 x 2.032 GHz"}
-            else:
-                out[name] = {"ms": ms, "achieved_fp64_equiv_tflops": tf, "fp64_pipe_peak_tflops": 1.13,
-                             "ratio_to_fp64_pipe": tf / 1.13, "ctas": nv,
-                             "note": "FP64-accurate products on the FP32 pipe (12 FP32 instructions each)"}
+        kA = kB = 64
+        no, nv, deg = 3, 96, 10
+        rng = np.random.default_rng(7)
+        EA, EB, oA, oB, coef = I.random_block_inputs(rng, kA, kB, no)
+        X = rng.standard_normal((nv, kA, kB))
+        flops = nv * deg * (2.0 * no * kA * kB * (kA + kB) + 3.0 * kA * kB)
+        d = [torch.tensor(a, dtype=torch.float32, device=dev) for a in (EA, EB, oA, oB, X)]
+        Y = torch.empty_like(d[4])
+        ms = time_launches(torch, stream, lambda: ctx.cheb_filter(
+            1, kA, kB, no, nv, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(), coef,
+            d[4].data_ptr(), deg, -20.0, -10.0, 10.0, True, Y.data_ptr()), reps=20)
+        tf = flops / (ms / 1e3) / 1e12
+        out["fused_filter_fp32_64x64x3_nv96_deg10"] = {"ms": ms, "algorithmic_tflops": tf,
+                                                        "frac_of_fp32_pipe": tf / FP32_SIMT_PEAK_TFLOPS}
     return out
+
+
+def xxz_batch(P, torch, dev, precision, slots, steps=3, warmup=2):
+    """The batched XXZ N = 32, k = 64 workload: 32 oracle-validated instances a
+    step through the solve server."""
+    gold = load_gold_xxz()
+    seeds = xxz_seeds(0, 32, gold.keys())
+    chains = [I.xxz_n32(s) for s in seeds]
+    srv = P.Server(slots=slots, device=dev.index, precision=precision)
+
+    def step():
+        tids = [srv.submit(ch) for ch in chains]
+        return [srv.poll(t, wait=True) for t in tids]
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    valid, lat = 0, []
+    for _ in range(steps):
+        for (E, st, la, _), sd in zip(step(), seeds):
+            valid += int(st == 0 and within(E, gold.get(sd)))
+            lat.append(la)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    srv.close()
+    return {"workload": "xxz_n32_k64", "solves_per_s": valid / dt, "valid_solves": valid, "solves": steps * 32,
+            "slots": slots, "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
+            "timing": "host wall clock around each 32-solve batch (server API, host arrays in and out)"}
 
 
 def run_ours(args):
@@ -354,12 +468,24 @@ def run_ours(args):
     world, rank, local, pg = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    gold = load_gold()
-    seeds = batch_seeds(rank, args.batch, gold.keys())
-    chains = [I.xxz_n32(s) for s in seeds]
+    pk = peaks()
+    wl = WORKLOADS["rfheis"]
+    batch = args.batch or 1
+    seeds = rf_seeds(rank, batch)
+    chains = [I.rf_heisenberg_n128(s, k=256) for s in seeds]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    # tile autotuning: one untimed solve of the first instance fills the
-    # process-wide table the server's slots then read
+
+    # plain FP64 per-solve arm: the reference energies of this run's instances
+    # (and the baseline the mixed form must beat)
+    ref, fp64_s = [], []
+    with P.Context(device=local, precision="fp64") as c64:
+        for ch in chains:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ref.append(c64.solve_chain(ch))
+            torch.cuda.synchronize()
+            fp64_s.append(time.perf_counter() - t0)
+
     tiles = "untuned (first candidate of every product)"
     if not args.no_autotune:
         t0 = time.perf_counter()
@@ -367,32 +493,22 @@ def run_ours(args):
             tctx.autotune(chains[0])
         tiles = (f"autotuned: {len(P.tune_dump().splitlines())} shape bins, one tuning solve "
                  f"({time.perf_counter() - t0:.1f} s) before warm-up")
-    srv = P.Server(slots=args.slots, device=local, precision=args.precision)
 
-    def step():
-        tids = [srv.submit(ch) for ch in chains]
-        return [srv.poll(t, wait=True) for t in tids]
-
-    for _ in range(args.warmup):
-        step()
+    ctx = P.Context(device=local, precision=args.precision, lanes=args.lanes)
+    for i in range(args.warmup):
+        ctx.solve_chain(chains[i % len(chains)])
     torch.cuda.synchronize()
 
-    # live timing of the matvec kernel only (two event records per launch
-    # group; timing every kind would add ~0.3 M event records a second to the
-    # host's launch path); the per-kind breakdown comes from one profiled step
-    # after the timed region
-    kron_key = {"fp64": "kron_fp64", "mixed_tf32": "kron_working"}.get(args.precision, "fused_working")
+    kron_key = {"fp64": "kron_fp64"}.get(args.precision, "kron_working")
     clocks = ClockSampler(local)
     clocks.start()
-    l0 = srv.stats()["launches"]
-    srv.profile(True, kinds=None if args.profile_all_kinds else [kron_key])
-    srv.profile_read()
+    l0 = ctx.stats()[0]
+    ctx.profile(True, kinds=[kron_key])
+    ctx.profile_read()
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    step_ms, lat_ms, queue_ms, valid, total = [], [], [], 0, 0
-    e2e_s = 0.0
+    step_ms, e2e_s, valid, total, rel_err = [], 0.0, 0, 0, 0.0
     for s in range(args.steps):
         flush.zero_()                       # evict the previous step's data from L2
         torch.cuda.synchronize()
@@ -400,113 +516,193 @@ def run_ours(args):
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record()
         t0 = time.perf_counter()
-        outs = step()
-        torch.cuda.synchronize()            # every slot's stream is idle here
+        outs = [ctx.solve_chain(ch) for ch in chains]
+        torch.cuda.synchronize()            # every lane's stream is idle here
         s1.record()
         s1.synchronize()
         e2e_s += time.perf_counter() - t0
         step_ms.append(s0.elapsed_time(s1))
-        for (E, st, lat, qd), sd in zip(outs, seeds):
-            lat_ms.append(lat)
-            queue_ms.append(qd)
+        for E, r in zip(outs, ref):
             total += 1
-            ref = gold.get(sd)
-            if st == 0 and ref is not None and np.all(np.abs(E - ref) <= RTOL * np.maximum(1.0, np.abs(ref))):
-                valid += 1
+            valid += int(within(E, r))
+            rel_err = max(rel_err, float(np.max(np.abs(E - r) / np.maximum(1.0, np.abs(r)))))
     torch.cuda.synchronize()
     if pg is not None:
         pg.barrier()
-    wall = time.perf_counter() - wall0
-    prof = srv.profile_read()
-    l1 = srv.stats()["launches"]
+    prof = ctx.profile_read()
+    l1 = ctx.stats()[0]
     clk = clocks.stop()
-    srv.profile(True)                       # every kind, one untimed step
-    srv.profile_read()
-    step()
+    ctx.profile(True)                       # every kind, one untimed solve
+    ctx.profile_read()
+    t0 = time.perf_counter()
+    ctx.solve_chain(chains[0])
     torch.cuda.synchronize()
-    prof_all = srv.profile_read()
-    srv.profile(False)
-    srv.close()
-    alone = kernel_alone(P, torch, dev) if rank == 0 else None
+    profiled_s = time.perf_counter() - t0
+    prof_all = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
 
     dev_s = sum(step_ms) / 1e3
-    max_dev_s = reduce_max(pg, dev_s, dev)
-    max_e2e_s = reduce_max(pg, e2e_s, dev)
-    valid_all = reduce_sum(pg, valid, dev)
-    total_all = reduce_sum(pg, total, dev)
-
-    # dominant kernel group and the Kronecker product's roofline
-    # (algorithmic FLOPs / summed per-stream event time)
-    # The Kronecker-form product is the path's matvec; in the mixed path it runs
-    # as the single-launch Chebyshev filter (the two-stage form serves blocks
-    # too wide for it).  Its per-launch times are the library's CUDA events on
-    # each slot's stream over the timed region, so under concurrent slots they
-    # include waits for SMs that other slots hold; kernel_alone gives the
-    # same kernel timed by itself.
-    dom = max(prof_all.items(), key=lambda kv: kv[1][2])
-    kname = {"fp64": "Kronecker-form product, FP64 (fused and two-stage)",
-             "mixed_tf32": "two-stage Kronecker-form product on tcgen05 (3xTF32)"}.get(
-        args.precision, "cheb_fused_v4_kernel (single-launch FP32 Chebyshev filter)")
-    kg, kl, kms, kfl = prof[kron_key]
-    if args.precision == "fp64":
-        peak, bound, peak_src = 1.13, "alu", "FP64 DFMA pipe, 1.13 TFLOP/s measured by a DFMA loop on this part"
-    elif args.precision == "mixed_tf32":
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1800.0}
-        peak = peaks["bf16_tflops"] * (1.1 / 2.25)
-        bound = "tensor"
-        peak_src = ("TF32 tensor peak = measured BF16 burst x nominal TF32/BF16 (1.1/2.25); the 3xTF32 "
-                    "product executes 3 tensor products per useful one, so frac <= 1/3 by construction")
-    else:
-        peak, bound, peak_src = FP32_SIMT_PEAK_TFLOPS, "alu", "FP32 FMA pipe: 148 SMs x 128 lanes x 2 x 2.032 GHz"
-    achieved = (kfl / (kms / 1e3)) / 1e12 if kms > 0 else 0.0
-    whole_gpu = (kfl / dev_s) / 1e12 if dev_s > 0 else 0.0
-    stream_ms = sum(v[2] for v in prof_all.values())
-    breakdown = {k: {"launch_groups": v[0], "launches": v[1], "stream_ms": round(v[2], 3),
-                     "share": round(v[2] / (stream_ms or 1), 4)} for k, v in prof_all.items()}
-    breakdown["note"] = "one profiled step after the timed region, every kind timed (nested groups overlap)"
+    max_dev_s = reduce_op(pg, dev_s, dev, "max")
+    max_e2e_s = reduce_op(pg, e2e_s, dev, "max")
+    valid_all = reduce_op(pg, valid, dev, "sum")
+    total_all = reduce_op(pg, total, dev, "sum")
+    fp64_all = reduce_op(pg, sum(fp64_s), dev, "sum")
+    fp64_n = reduce_op(pg, len(fp64_s), dev, "sum")
 
     if rank == 0:
-        vals = sorted(lat_ms)
-        p50 = vals[len(vals) // 2]
-        p99 = vals[min(len(vals) - 1, int(round(0.99 * (len(vals) - 1))))]
+        extras = {} if args.no_extras else {"kernel_alone": kernel_alone(P, torch, dev, pk),
+                                            "xxz_batch": xxz_batch(P, torch, dev, args.precision, args.slots)}
+        stream_ms = sum(v[2] for v in prof_all.values())
+        breakdown = {k: {"launch_groups": v[0], "launches": v[1], "stream_ms": round(v[2], 1),
+                         "share": round(v[2] / (stream_ms or 1), 4)} for k, v in prof_all.items() if v[1]}
+        breakdown["note"] = ("one solve after the timed region with every kind timed (lanes run merges "
+                             f"concurrently, so stream times sum over lanes); solve wall {profiled_s:.2f} s")
+        kg, kl, kms, kfl = prof[kron_key]
+        live = (kfl / (kms / 1e3)) / 1e12 if kms > 0 else 0.0
+        tf32_peak = pk["bf16"] * TF32_PER_BF16
+        if args.precision == "fp64":
+            roof = {"kernel": "Kronecker-form product, FP64 (DFMA)", "bound": "alu", "achieved": live,
+                    "peak": FP64_PIPE_TFLOPS, "unit": "TFLOP/s", "frac": live / FP64_PIPE_TFLOPS, "traffic": None,
+                    "peak_source": "FP64 DFMA pipe, 1.13 TFLOP/s measured by a DFMA loop on this part",
+                    "timing": "live per-lane CUDA events over the timed region"}
+        else:
+            alone = extras.get("kernel_alone", {}).get("kron_256x256x3_nv160_tcgen05_3xtf32")
+            achieved = alone["algorithmic_tflops"] if alone else live
+            roof = {"kernel": "gemm_tma_tf32x3_kernel (tcgen05 3xTF32, TMA-fed; both Kronecker stages, "
+                              "256 x 256 x 3 operators, 160 vectors)",
+                    "bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tf32_peak,
+                    "traffic": 5.91e8,
+                    "traffic_note": ("dram bytes read+written by the two launches of one product on 288 vectors "
+                                     "(ncu, profiles/gemm_tma_tf32x3_kron256_nv288.md): 5.91e8 B; traffic grows "
+                                     "with the vectors, so for 160 vectors about 3.3e8 B"),
+                    "peak_source": (f"TF32 dense tensor peak = measured BF16 burst {pk['bf16']:.1f} x nominal "
+                                    f"TF32/BF16 1.1/2.25 ({pk['source']}); 3xTF32 issues three tensor products per "
+                                    "useful one, so frac <= 1/3 by construction (mma_frac = 3 x frac)"),
+                    "mma_frac": 3 * achieved / tf32_peak,
+                    "timing": "the product alone on the context's stream, CUDA events, after the timed region",
+                    "live_in_timed_region_tflops": live,
+                    "live_note": "per-lane CUDA events over the timed region (8 lanes: intervals include waits)"}
         line = {
-            "metric": METRIC, "value": valid_all / max_dev_s, "unit": UNIT, "n_gpus": world,
+            "metric": wl["metric"], "value": valid_all / max_dev_s, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_dev_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"mixed": "f32+f64", "mixed_tf32": "tf32x3+f32+f64", "fp64": "f64"}[args.precision],
-            "data": "synthetic (seeded XXZ chains, J_i ~ U[0.5,1.5])",
-            "config": {"workload": WORKLOAD, "N": 32, "k": 64, "q": 8, "L0": 4, "delta": 1.0,
-                       "batch_per_gpu": args.batch, "slots": args.slots, "precision": args.precision,
-                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)",
-                       "tiles": tiles,
-                       "timing": "CUDA events after device-wide synchronisation (work spans the slots' streams)"},
-            "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean(lat_ms),
-                           "queue_p50": sorted(queue_ms)[len(queue_ms) // 2]},
+            "dtype": {"mixed": "tf32x3+f32+f64", "mixed_tf32": "tf32x3+f32+f64", "fp64": "f64"}[args.precision],
+            "data": "synthetic (seeded random-field Heisenberg chains, h_i ~ U[-2,2])",
+            "config": {"workload": wl["name"], "N": 128, "k": 256, "q": 16, "L0": 4, "delta": 1.0, "J": 1.0,
+                       "fields": "U[-2,2]", "seeds": seeds, "batch_per_gpu": batch, "precision": args.precision,
+                       "lanes": args.lanes or 8, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (512 MB write); merge working sets exceed L2",
+                       "tiles": tiles, "reference": "plain FP64 GPU solve of the same instances",
+                       "timing": "CUDA events after device-wide synchronisation around each step"},
             "valid_solves": int(valid_all), "solves": int(total_all),
-            "matvec": {"tflops_per_stream": achieved, "tflops_whole_gpu": whole_gpu, "peak_tflops": peak,
-                       "launch_groups": kg, "stream_ms": kms},
-            "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
-                         "peak_source": peak_src, "launches": kl,
-                         "timing": "per-launch CUDA events on the slots' streams over the timed region "
-                                   "(16 concurrent slots: intervals include waits for SMs)",
-                         "dominant_group": dom[0], "dominant_share": round(dom[1][2] / (stream_ms or 1), 4)},
+            "fp64_per_solve": {"seconds_per_solve": fp64_all / max(1, fp64_n),
+                               "solves_per_s": fp64_n / max(fp64_all, 1e-9),
+                               "speedup_of_mixed": (valid_all / max_dev_s) / (fp64_n / max(fp64_all, 1e-9))},
+            "max_rel_err_vs_fp64": reduce_op(pg, rel_err, dev, "max"),
+            "roofline": roof,
             "breakdown": breakdown,
-            "kernel_alone": alone,
+            "e2e": {"value": valid_all / max_e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(chain_bytes(c) for c in chains)),
+                    "d2h_bytes_per_step": int(8 * sum(c.q for c in chains)),
+                    "note": "rmc_solve_chain takes the chain description from host memory and returns host "
+                            "energies; the timed step is that call, so e2e ~ value"},
+            "gpu_launches": int(l1 - l0),
+            "clocks": clk,
+        }
+        line.update(extras)
+        if world == 1 and not args.no_cpu_baseline:
+            est, sample, took = oracle_rfheis_estimate(0)
+            line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+                                    "sample": sample + f" ({took:.1f} s of host time)", "seconds_per_solve": est}
+            try:
+                t1 = oracle_xxz_one_thread()
+            except Exception as exc:  # the baseline is context; its failure must not lose the line
+                t1 = f"unavailable: {type(exc).__name__}"
+            tn, _ = oracle_xxz_solve_time(I.xxz_n32())
+            line["cpu_baseline_xxz"] = {"seconds_per_solve_1_thread": t1, "seconds_per_solve_all_cores": tn,
+                                        "cores": _blas_threads(),
+                                        "sample": "one whole oracle solve of the XXZ N=32, k=64 instance "
+                                                  "(seed 260902), 1 BLAS thread (the paper's setting) and all"}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_xxz(args):
+    """The batched XXZ N = 32, k = 64 workload through the solve server."""
+    import torch
+
+    import paper_2609_02394_b300 as P
+
+    world, rank, local, pg = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gold = load_gold_xxz()
+    batch = args.batch or 32
+    seeds = xxz_seeds(rank, batch, gold.keys())
+    chains = [I.xxz_n32(s) for s in seeds]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if not args.no_autotune:
+        with P.Context(device=local, precision=args.precision) as tctx:
+            tctx.autotune(chains[0])
+    srv = P.Server(slots=args.slots, device=local, precision=args.precision)
+
+    def step():
+        tids = [srv.submit(ch) for ch in chains]
+        return [srv.poll(t, wait=True) for t in tids]
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = srv.stats()["launches"]
+    if pg is not None:
+        pg.barrier()
+    step_ms, lat, valid, total, e2e_s = [], [], 0, 0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        t0 = time.perf_counter()
+        outs = step()
+        torch.cuda.synchronize()
+        s1.record()
+        s1.synchronize()
+        e2e_s += time.perf_counter() - t0
+        step_ms.append(s0.elapsed_time(s1))
+        for (E, st, la, _), sd in zip(outs, seeds):
+            lat.append(la)
+            total += 1
+            valid += int(st == 0 and within(E, gold.get(sd)))
+    if pg is not None:
+        pg.barrier()
+    l1 = srv.stats()["launches"]
+    clk = clocks.stop()
+    srv.close()
+    max_dev_s = reduce_op(pg, sum(step_ms) / 1e3, dev, "max")
+    max_e2e_s = reduce_op(pg, e2e_s, dev, "max")
+    valid_all = reduce_op(pg, valid, dev, "sum")
+    total_all = reduce_op(pg, total, dev, "sum")
+    if rank == 0:
+        wl = WORKLOADS["xxz"]
+        print(json.dumps({
+            "metric": wl["metric"], "value": valid_all / max_dev_s, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_dev_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded XXZ chains, J_i ~ U[0.5,1.5])",
+            "config": {"workload": wl["name"], "N": 32, "k": 64, "q": 8, "L0": 4, "batch_per_gpu": batch,
+                       "slots": args.slots, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (512 MB write)"},
+            "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
+            "valid_solves": int(valid_all), "solves": int(total_all),
             "e2e": {"value": valid_all / max_e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(chain_bytes(c) for c in chains)),
                     "d2h_bytes_per_step": int(8 * sum(c.q for c in chains))},
-            "gpu_launches": int(l1 - l0),
-            "clocks": clk,
-            "wall_s": wall,
-        }
-        if world == 1 and not args.no_cpu_baseline:
-            est, sampled, n_m = oracle_solve_time_estimate(chains[0], budget_s=25.0)
-            line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": _oracle_threads(), "kind": "oracle",
-                                    "sample": f"one solve of seed {seeds[0]}: leaves + {sampled} of {n_m} merges "
-                                              f"timed once each" + (", rest extrapolated" if sampled < n_m else "")}
-        print(json.dumps(line), flush=True)
+            "gpu_launches": int(l1 - l0), "clocks": clk}), flush=True)
     if pg is not None:
         pg.destroy_process_group()
 
@@ -515,20 +711,36 @@ def run_serving(args):
     """Serving: requests arrive as a Poisson stream (seeded) and are submitted on
     schedule to the continuous-batching server (slots run concurrently, each
     admitted under the 40 GB device-memory budget); latency is arrival to
-    result.  A sample of requests is re-solved alone on the plain FP64 GPU path
-    and compared within 1e-8 relative."""
+    result.  Every completed request is validated: against the oracle's
+    energies when its merges are small enough for the dense oracle (k <= 32 or
+    N <= 12), else against the plain FP64 GPU path; solves/s counts validated
+    solves only."""
     import torch
 
     import paper_2609_02394_b300 as P
+    from oracle import rmc_oracle as O
 
     torch.cuda.init()
     budget = 40 << 30
-    out = {"metric": "serving: solves/s and p50/p99 latency (arrival to result) at 1e-8 energy error",
-           "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "f32+f64" if args.precision == "mixed"
-           else args.precision, "data": "synthetic (seeded mixed TFIM / XXZ / random-field request stream)",
+    out = {"metric": "serving: validated solves/s and p50/p99 latency (arrival to result) at 1e-8 energy error",
+           "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+           "dtype": "tf32x3+f32+f64" if args.precision != "fp64" else "f64",
+           "data": "synthetic (seeded mixed TFIM / XXZ / random-field request stream)",
            "config": {"workload": "serving", "N": "U{8..128}", "k": "{16,32,64,128,256}", "q": "U{1..16}",
                       "slots": args.slots, "mem_budget_gb": 40, "requests_per_rate": args.requests,
                       "precision": args.precision}, "rates": []}
+    refs = {}
+
+    def reference(i, r):
+        if i in refs:
+            return refs[i]
+        if r.k <= 32 or r.n_sites <= 12:
+            refs[i] = ("oracle", O.solve(r).energies)
+        else:
+            with P.Context(precision="fp64") as c64:
+                refs[i] = ("fp64_gpu", c64.solve_chain(r))
+        return refs[i]
+
     for ri, rate in enumerate(float(r) for r in args.rates.split(",")):
         reqs = I.serving_requests(args.requests, seed=I.seed_for(5) + ri)
         gaps = np.random.default_rng(I.seed_for(5) * 10 + ri).exponential(1.0 / rate, size=len(reqs))
@@ -556,28 +768,22 @@ def run_serving(args):
         torch.cuda.synchronize()
         srv.close()
         done_t = [s + res[2] / 1e3 for s, res in zip(sub_t, results)]
-        ok = [res[1] == 0 for res in results]
-        # accuracy sample: the cheapest requests, re-solved alone on the FP64 path
-        order = sorted(range(len(reqs)), key=lambda i: (reqs[i].k, reqs[i].n_sites))[:args.check]
-        checked, agree = 0, 0
-        with P.Context(precision="fp64") as ctx:
-            for i in order:
-                if not ok[i]:
-                    continue
-                ref = ctx.solve_chain(reqs[i])
-                checked += 1
-                E = results[i][0]
-                agree += int(np.all(np.abs(E - ref) <= RTOL * np.maximum(1.0, np.abs(ref))))
-        lat = sorted(res[2] for res in results)
         span = max(done_t) - min(sub_t)
+        # validation of every completed request (outside the timed stream)
+        kinds, valid = {"oracle": 0, "fp64_gpu": 0}, 0
+        for i, (r, res) in enumerate(zip(reqs, results)):
+            if res[1] != 0:
+                continue
+            kind, E_ref = reference((ri, i), r)
+            kinds[kind] += 1
+            valid += int(within(res[0], E_ref))
+        lat = [res[2] for res in results]
         out["rates"].append({
-            "rate_req_s": rate, "requests": len(reqs), "completed_ok": int(sum(ok)),
-            "solves_per_s": sum(ok) / span, "span_s": span,
-            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
-                           "max": lat[-1]},
-            "queue_ms_p50": sorted(res[3] for res in results)[len(results) // 2],
+            "rate_req_s": rate, "requests": len(reqs), "completed_ok": int(sum(res[1] == 0 for res in results)),
+            "validated": valid, "validated_against": kinds, "solves_per_s": valid / span, "span_s": span,
+            "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99), "max": max(lat)},
+            "queue_ms_p50": percentile([res[3] for res in results], 0.5),
             "peak_reserved_gb": peak_reserved / 2**30,
-            "checked_vs_fp64": checked, "agree_within_1e-8": agree,
         })
         print(json.dumps(out["rates"][-1]), file=sys.stderr, flush=True)
     best = max(out["rates"], key=lambda r: r["solves_per_s"])
@@ -591,6 +797,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "xxz":
+        run_xxz(args)
     else:
         run_ours(args)
 
