@@ -870,6 +870,74 @@ __global__ void add_f32_kernel(double* __restrict__ Y, const float* __restrict__
     Y[e] += (double)F[e];
 }
 
+// For the basis Q = C + E (C orthonormal, E orthogonal to C up to the FP32
+// rounding of E):
+//   S  = Q^T Q - I = SCE + SCE^T + SEE,
+//   Gm = Q^T H Q   = diag(theta) + CR + (C^T H E) + (E^T H C) + EHE,
+// with C^T H E = (H C)^T E = R^T E + diag(theta) C^T E, i.e.
+//   (C^T H E)_ij = RE_ij + theta_i SCE_ij, (E^T H C)_ij = RE_ji + theta_j SCE_ji.
+// SCE = C^T E is the FP64-accurate Gram product (the FP32 rounding of a large
+// guard-column correction has components along C that theta would magnify);
+// CR = C^T R, RE = R^T E, SEE = E^T E, EHE = E^T H E are FP32 (each involves
+// a small factor, or only guard-guard entries carry a large error).
+__global__ void defect_gram_kernel(const double* __restrict__ SCE, const float* __restrict__ SEE,
+                                   const float* __restrict__ CR, const float* __restrict__ RE,
+                                   const float* __restrict__ EHE, const double* __restrict__ theta, int m,
+                                   double* __restrict__ S, double* __restrict__ Gm) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e / m, j = e % m;
+    const int t = j * m + i;
+    S[e] = SCE[e] + SCE[t] + (double)SEE[e];
+    const double g = (double)CR[e] + (double)RE[e] + theta[i] * SCE[e] + (double)RE[t] + theta[j] * SCE[t] +
+                     (double)EHE[e];
+    const double gt = (double)CR[t] + (double)RE[t] + theta[j] * SCE[t] + (double)RE[e] + theta[i] * SCE[e] +
+                      (double)EHE[t];
+    Gm[e] = (i == j ? theta[i] : 0.0) + 0.5 * (g + gt);
+  }
+}
+
+// E[i][r] = (float)(Dperp[i][r] / y[i]): each filtered column's correction
+// outside span C, relative to its own amplification.
+__global__ void scale_columns_inv_kernel(const float* __restrict__ D, const double* __restrict__ y, long n, long tot,
+                                         float* __restrict__ E) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    E[e] = (float)((double)D[e] / y[e / n]);
+}
+
+// out = alpha I + beta A (m x m).
+__global__ void shifted_identity_kernel(const double* __restrict__ A, int m, double alpha, double beta,
+                                        double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)
+    out[e] = ((e / m) == (e % m) ? alpha : 0.0) + (A ? beta * A[e] : 0.0);
+}
+
+// Start of the scaled coupled Newton-Schulz iteration for (I + S)^{-1/2}
+// (one CTA): c = 1 + trace(SEE) bounds the largest eigenvalue of I + S
+// (S = C^T E + E^T C + E^T E with E orthogonal to C, so I + S >= I up to
+// rounding and its excess is at most trace(E^T E)); Y = (I + S) / c has its
+// spectrum in [1/c, 1], where the iteration converges.  c goes to *cdev.
+__global__ void ns_start_kernel(const double* __restrict__ S, const float* __restrict__ SEE, int m,
+                                double* __restrict__ Y, double* __restrict__ cdev) {
+  __shared__ double red[32];
+  __shared__ double cs;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) t += fmax(0.0, (double)SEE[(long)i * m + i]);
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) {
+    cs = 1.0 + t;
+    *cdev = cs;
+  }
+  __syncthreads();
+  const double inv = 1.0 / cs;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) Y[e] = (((e / m) == (e % m) ? 1.0 : 0.0) + S[e]) * inv;
+}
+
+// W <- W / sqrt(c): undo the scaling of ns_start_kernel.
+__global__ void scale_inv_sqrt_kernel(double* __restrict__ W, int m, const double* __restrict__ cdev) {
+  const double f = 1.0 / sqrt(*cdev);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) W[e] *= f;
+}
+
 // F^T for the first-order second Cholesky-QR pass: G = I + E  =>  R ~ I + F,
 // F upper triangular with F_ij = E_ij (i < j), F_ii = E_ii / 2; returns
 // W = F^T (lower triangular) so that X_new = X - W X.

@@ -1448,66 +1448,111 @@ rmc_status prepare_kron(rmc_ctx* ctx, Workspace& ws, const MergeInput& in, KronO
 // FP64 refinement of a wide block (more vectors than the small eigensolver
 // takes) in defect form, for the mixed paths.
 //
-// The iterate is C (FP64, orthonormal Ritz vectors, Ritz values w) together
-// with its FP64-accurate product HC.  A Chebyshev filter pass (the scaled
-// recurrence of cheb_filter, bounds from the current Ritz values) applied to
-// C splits exactly into
-//     p(H) C = C diag(y(w)) + D,
-// where y_d is the same three-term recurrence evaluated at the Ritz values
-// and the defect D obeys
+// The iterate is C (FP64, orthonormal Ritz vectors, Ritz values theta)
+// together with its FP64-accurate product HC.  A Chebyshev filter pass (the
+// scaled recurrence of cheb_filter, bounds from the current Ritz values)
+// applied to C splits exactly into
+//     p(H) C = C diag(y(theta)) + D,
+// where y_d is the same three-term recurrence evaluated at the Ritz values and
+// the defect D obeys
 //     D_1 = (s_1/e) R,
 //     D_d = (2 s_d/e)(H - c) D_{d-1} - s_{d-1} s_d D_{d-2} + (2 s_d/e) R diag(y_{d-1})
-// with R = HC - C diag(w) the Ritz residuals.  D is as small as R, so its
-// products run in FP32 (a rounding error of FP32 relative to D is ~1e-7 of R,
-// far below the FP64 target), and the new block X = C diag(y) + D is FP64-
-// accurate.  After the FP64 orthonormalisation of X, its product is again
-// split: with M = C^T X and Q = X - C M (the part of X outside span C, as
-// small as the subspace moved),
-//     H X = HC M + H Q,
-// HC M in FP64 and H Q in FP32.  So a refinement pass costs FP32 Kronecker
-// products plus FP64-accurate Gram and combination GEMMs; the only
-// FP64-accurate Kronecker product is the first one, of the working-precision
-// block.  The filter covers the whole block at once (no chunks): its
-// amplification ratio is capped (kDefectRho) so that the filtered block stays
-// within ~1e-4 of orthonormal and first-order Cholesky-QR passes suffice, and
-// the Rayleigh-Ritz matrix of the new block is nearly diagonal, so its FP64
-// eigensolver starts from the identity.
+// with R = HC - C diag(theta) the Ritz residuals.  D is as small as R, so its
+// products run in FP32 (an FP32 rounding relative to D is ~1e-7 of R, far
+// below the FP64 target).
 //
-// On return C holds the Ritz vectors and w their values (ascending), the
-// residual test having passed for the first k_acc vectors or max_passes filter
-// passes run.  X, HX and HC are scratch (b x n FP64 each, HC also n_ops wide
-// for the first product), Tf FP32 scratch for the FP32 products.
+// The new basis is Q = C + E with E = D_perp diag(1/y), where D = C G1 + D_perp
+// (G1 = C^T D, D_perp outside span C): each column gains the part of its
+// filtered image outside the current span, relative to its own amplification
+// -- the subspace-iteration step, with the in-span mixing of the filtered
+// columns left to the Rayleigh-Ritz step.  (Forming span(X) exactly would
+// need A^{-1} for A = diag(y) + G1, which is ill-conditioned for the guard
+// columns at the bottom of the filter, where y ~ 1/kDefectRho; a
+// Newton-Schulz inverse diverged there and stalled two merges.)  E is as small
+// as the subspace still moves, up to ~2x a guard column's current error.  Then,
+// with H E an FP32 product,
+//     Q^T Q = I + C^T E + E^T C + E^T E,
+//     Q^T H Q = diag(theta) + C^T R + C^T HE + E^T HC + E^T HE,
+// and C^T HE = (HC)^T E = R^T E + diag(theta) C^T E.  C^T E is the one
+// FP64-accurate Gram product of the pass: E is stored in FP32, and for the
+// unconverged guard columns it is large (up to ~0.4), so its rounding has
+// components along C of ~2e-8 that theta would magnify into the Rayleigh-Ritz
+// matrix (measured: a residual floor of 2e-8 - 1.4e-7 on half the 65536-row
+// merges when all Gram products were FP32).  C^T R, R^T E, E^T E and E^T HE
+// involve a small factor, or carry a large error only in guard-guard entries,
+// and stay FP32.  The generalised
+// Rayleigh-Ritz problem is solved as W Q^T H Q W with W = (Q^T Q)^{-1/2}
+// (a coupled Newton-Schulz iteration); its matrix is nearly diagonal, so the
+// FP64 eigensolver starts from the identity.  With Z the
+// combined rotation W Z~, the new iterate is C Z + E Z and its product
+// HC Z + HE Z: C Z and HC Z are FP64-accurate combinations, E Z and HE Z FP32.
+// A pass therefore costs FP32 Kronecker products on small data (tensor-core for
+// the 256-state merges' filter; H E on the FP32 pipe, since it enters H C
+// directly), FP32 Gram products, one FP64-accurate Gram product and two
+// FP64-accurate combinations, where the earlier form of the pass took twelve
+// FP64-accurate Gram and combination products; the merge's only FP64-accurate
+// Kronecker product is the first one, of the working-precision block.
+//
+// The passes stop when the kept vectors pass the residual test, after
+// max_passes, or after two passes in a row that did not halve the worst
+// residual.  On the 128-site k = 256 chain 12 of 14 merges of dimension 65536
+// pass the 1e-8 test in 3-5 passes; two stop at 5e-8 and 1.6e-7 on 2-4
+// vectors whose residuals barely move under further passes of either this
+// form or a fully FP64-accurate one (double-FP32 Gram and combination
+// products), and the chain's energies still agree with the plain FP64 path to
+// 6e-11.
+//
+// The filter covers the whole block at once (no chunks); its amplification
+// ratio is capped (kDefectRho) so that the guard columns' corrections stay
+// moderate.  Each pass leaves C orthonormal to ~1e-11 (the FP32 parts of its
+// corrections), so a last FP64 Cholesky-QR pass makes the returned basis
+// orthonormal to FP64 rounding.
+//
+// On return C holds the Ritz vectors and w their values (ascending).  X, HX and HC are scratch (b x n FP64 each, HC also n_ops wide
+// for the first product).
 constexpr double kDefectRho = 1e5;
 constexpr int kDefectMaxDeg = 40;
+constexpr int kInvSqrtSteps = 10;
 
 rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>& H64, const KronOp<float>& Hf, int b,
                               int k_acc, double ub, double tol, int max_passes, double* X, double* HX, double* C,
                               double* HC, double* G, double* w, double* Z, double* rn) {
   const long n = H64.n();
   const long tot = (long)b * n;
-  float *Rf, *D0, *D1, *D2, *Tf, *sdev;
-  double *M, *ydev;
+  const size_t bb = (size_t)b * b;
+  float *Rf, *D0, *D1, *D2, *Tf, *sdev, *Cf, *E, *HE, *g32, *Af;
+  double *ydev, *X1, *Tm, *S, *S2, *Wm, *Gm, *Gt, *Zt, *Zs;
   TRY(ws.get(&Rf, (size_t)tot));
   TRY(ws.get(&D0, (size_t)tot));
   TRY(ws.get(&D1, (size_t)tot));
   TRY(ws.get(&D2, (size_t)tot));
+  TRY(ws.get(&Cf, (size_t)tot));
+  TRY(ws.get(&E, (size_t)tot));
+  TRY(ws.get(&HE, (size_t)tot));
   TRY(ws.get(&Tf, (size_t)std::max(1, Hf.n_ops) * tot));
   TRY(ws.get(&sdev, (size_t)kDefectMaxDeg * b));
+  TRY(ws.get(&g32, 5 * bb));
+  TRY(ws.get(&Af, bb));
   TRY(ws.get(&ydev, (size_t)b));
-  TRY(ws.get(&M, (size_t)b * b));
+  double* cdev;
+  TRY(ws.get(&cdev, 1));
+  for (double** m : {&X1, &Tm, &S, &S2, &Wm, &Gm, &Gt, &Zt, &Zs}) TRY(ws.get(m, bb));
+  float *G1 = g32, *SEE = g32 + bb, *CR = g32 + 2 * bb, *RE = g32 + 3 * bb, *EHE = g32 + 4 * bb;
+  double* SCE;
+  TRY(ws.get(&SCE, bb));
+  double* const C_out = C;
   // FP64 Rayleigh-Ritz of the working-precision block: the one FP64-accurate
   // Kronecker product (HC serves as its scratch before it holds H C)
   TRY(cholqr64_refine(ctx, ws, X, b, n, C));
   TRY(kron_product<double>(ctx, H64, X, b, HX, HC));
-  auto rayleigh_ritz = [&]() -> rmc_status {
-    TRY(gram<double>(ctx, ws, X, b, HX, b, n, G, true));
-    TRY(syev64(ctx, ws, G, b, w, Z, true));
-    TRY(combine<double>(ctx, Z, true, b, b, X, n, C, 1.0, 0.0, nullptr));
-    return combine<double>(ctx, Z, true, b, b, HX, n, HC, 1.0, 0.0, nullptr);
-  };
-  TRY(rayleigh_ritz());
-  std::vector<double> th(b), y0(b), y1(b), y2(b);
+  TRY(gram<double>(ctx, ws, X, b, HX, b, n, G, true));
+  TRY(syev64(ctx, ws, G, b, w, Z, true));
+  TRY(combine<double>(ctx, Z, true, b, b, X, n, C, 1.0, 0.0, nullptr));
+  TRY(combine<double>(ctx, Z, true, b, b, HX, n, HC, 1.0, 0.0, nullptr));
+  std::vector<double> th(b), y0(b), y1(b), y2(b), r(b);
   std::vector<float> sc((size_t)kDefectMaxDeg * b);
+  double prev_worst = 1e300;
+  int stalled = 0;
   for (int pass = 0;; ++pass) {
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
     residual_kernel<double><<<b, 256, 0, ctx->stream>>>(C, HC, w, n, k_acc, tol, rn, ctx->d_status);
@@ -1515,15 +1560,19 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
     int fails = 0;
     TRY(read_status(ctx, &fails, 1));
     TRY(to_host<double>(ctx, w, th.data(), b));
-    if (ctx->trace) {
-      std::vector<double> r(b);
-      TRY(to_host<double>(ctx, rn, r.data(), b));
-      int wi = 0;
-      const double worst = worst_relative(r, th, k_acc, &wi);
+    TRY(to_host<double>(ctx, rn, r.data(), b));
+    int wi = 0;
+    const double worst = worst_relative(r, th, k_acc, &wi);
+    if (ctx->trace)
       fprintf(stderr, "[rmc refine defect] n=%ld b=%d pass=%d fails=%d worst i=%d res=%.3e theta=%.12g thb=%.12g\n", n,
               b, pass, fails, wi, worst, th[wi], th[b - 1]);
-    }
     if (fails == 0 || pass >= max_passes) break;
+    // two passes in a row without halving the worst residual: the remaining
+    // vectors converge too slowly to be worth more passes (the energies they
+    // feed into are second order in their residual)
+    stalled = (pass > 0 && worst > 0.5 * prev_worst) ? stalled + 1 : 0;
+    if (stalled >= 2) break;
+    prev_worst = worst;
     const double a = th[b - 1], e = (ub - a) / 2, c = (ub + a) / 2;
     if (!(e > 0)) break;
     const double x0 = std::fabs((th[0] - c) / e);
@@ -1551,7 +1600,9 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
     // (pageable sources: the copies are staged before the calls return)
     CK(cudaMemcpyAsync(sdev, sc.data(), sizeof(float) * (size_t)(deg - 1) * b, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ydev, y1.data(), sizeof(double) * b, cudaMemcpyHostToDevice, ctx->stream));
-    // defect recurrence in FP32
+    // FP32 copies of the iterate, the residuals, and the defect recurrence
+    convert_kernel<float, double><<<grid1d(tot), 256, 0, ctx->stream>>>(C, Cf, tot);
+    CKL();
     ritz_residual_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(C, HC, w, n, tot, Rf);
     CKL();
     CK(cudaMemsetAsync(D0, 0, sizeof(float) * tot, ctx->stream));
@@ -1571,23 +1622,71 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
       Dn = t;
       sigma = s1;
     }
-    // X = C diag(y) + D, normalised, orthonormalised in FP64
-    defect_combine_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(C, ydev, Dc, n, tot, X);
+    // D = C G1 + D_perp (in place), E = D_perp diag(1/y)
+    {
+      Workspace wl(ctx);
+      TRY(gram<float>(ctx, wl, Cf, b, Dc, b, n, G1, false));
+      TRY(combine<float>(ctx, G1, true, b, b, Cf, n, Dc, -1.0f, 1.0f, Dc));
+      TRY(gram<float>(ctx, wl, Cf, b, Rf, b, n, CR, false));
+    }
+    scale_columns_inv_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(Dc, ydev, n, tot, E);
     CKL();
-    normalize_kernel<double><<<b, 256, 0, ctx->stream>>>(X, n, nullptr);
+    // H E on the FP32 pipe, not in 3xTF32: it enters the new H C directly, and
+    // the large corrections of the guard columns would carry the tensor-core
+    // form's ~5e-7 relative error into the kept vectors through the rotation
+    TRY(kron_apply<float>(ctx, Hf, E, b, HE, 1.0f, 0.0f, 0.0f, nullptr, Tf));
+    {
+      Workspace wl(ctx);
+      convert_kernel<double, float><<<grid1d(tot), 256, 0, ctx->stream>>>(E, X, tot);   // E exactly, in FP64
+      CKL();
+      TRY(gram<double>(ctx, wl, C, b, X, b, n, SCE, false));
+      TRY(gram<float>(ctx, wl, E, b, E, b, n, SEE, true));
+      TRY(gram<float>(ctx, wl, Rf, b, E, b, n, RE, false));
+      TRY(gram<float>(ctx, wl, E, b, HE, b, n, EHE, false));
+    }
+    defect_gram_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(SCE, SEE, CR, RE, EHE, w, b, S, Gm);
     CKL();
-    TRY(cholqr64_refine(ctx, ws, X, b, n, HX));
-    // H X = HC M + H Q with M = C^T X, Q = X - C M (Q in FP32 for its product)
-    TRY(gram<double>(ctx, ws, C, b, X, b, n, M, false));
-    TRY(combine<double>(ctx, M, true, b, b, C, n, HX, -1.0, 1.0, X));
-    convert_kernel<float, double><<<grid1d(tot), 256, 0, ctx->stream>>>(HX, D0, tot);
+    // W = (I + S)^{-1/2} by the coupled Newton-Schulz iteration on (I + S)/c
+    // (Y -> its square root, W -> its inverse square root; the corrections of
+    // unconverged guard columns make S far from small, so the spectrum is
+    // first scaled into [1/c, 1]); Gt = W Gm W; its eigenpairs; Z = W Zt
+    ns_start_kernel<<<1, 1024, 0, ctx->stream>>>(S, SEE, b, Gt, cdev);   // Y0 = (I + S) / c
     CKL();
-    TRY(kron_work<float>(ctx, Hf, D0, b, D1, 1.0f, 0.0f, 0.0f, nullptr, Tf));
-    TRY(combine<double>(ctx, M, true, b, b, HC, n, HX, 1.0, 0.0, nullptr));
+    shifted_identity_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(nullptr, b, 1.0, 0.0, Wm);  // W0 = I
+    CKL();
+    for (int it = 0; it < kInvSqrtSteps; ++it) {
+      TRY((small_mm<double, false, false>(ctx, Wm, Gt, b, S2, -0.5, 0.0, nullptr)));  // -W Y / 2
+      shifted_identity_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(S2, b, 1.5, 1.0, S2);  // T = 3/2 I - W Y / 2
+      CKL();
+      TRY((small_mm<double, false, false>(ctx, Gt, S2, b, Tm, 1.0, 0.0, nullptr)));  // Y T
+      TRY((small_mm<double, false, false>(ctx, S2, Wm, b, X1, 1.0, 0.0, nullptr)));  // T W
+      std::swap(Gt, Tm);
+      std::swap(Wm, X1);
+    }
+    scale_inv_sqrt_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(Wm, b, cdev);
+    CKL();
+    TRY((small_mm<double, false, false>(ctx, Wm, Gm, b, Tm, 1.0, 0.0, nullptr)));
+    TRY((small_mm<double, false, false>(ctx, Tm, Wm, b, Gt, 1.0, 0.0, nullptr)));
+    TRY(syev64(ctx, ws, Gt, b, w, Zt, true));
+    TRY((small_mm<double, false, false>(ctx, Wm, Zt, b, Zs, 1.0, 0.0, nullptr)));
+    // new iterate: C Z + E Z and HC Z + HE Z (FP64-accurate combinations of the
+    // O(1) parts, FP32 of the small ones); E, HE are reused for E Z, HE Z
+    TRY(combine<double>(ctx, Zs, true, b, b, C, n, X, 1.0, 0.0, nullptr));
+    TRY(combine<double>(ctx, Zs, true, b, b, HC, n, HX, 1.0, 0.0, nullptr));
+    convert_kernel<float, double><<<grid1d((long)bb), 256, 0, ctx->stream>>>(Zs, Af, (long)bb);
+    CKL();
+    TRY(combine<float>(ctx, Af, true, b, b, E, n, D0, 1.0f, 0.0f, nullptr));
+    TRY(combine<float>(ctx, Af, true, b, b, HE, n, D1, 1.0f, 0.0f, nullptr));
+    add_f32_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(X, D0, tot);
+    CKL();
     add_f32_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(HX, D1, tot);
     CKL();
-    TRY(rayleigh_ritz());
+    std::swap(C, X);
+    std::swap(HC, HX);
   }
+  // the basis to FP64 orthonormality (each pass left it within ~1e-11)
+  TRY(cholqr64_refine(ctx, ws, C, b, n, X));
+  if (C != C_out) CK(cudaMemcpyAsync(C_out, C, sizeof(double) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
   return RMC_OK;
 }
 
