@@ -76,6 +76,20 @@ struct EpiKron1T {  // m = v*kA + a, n = j*kB + b  ->  T'[(v*kB + b)*(n_ops*kA) 
     const int v = m / kA, a = m % kA, j = n / kB, b = n % kB;
     Tbuf[((long)v * kB + b) * ((long)n_ops * kA) + (long)j * kA + a] = acc;
   }
+  // The 32 x 32 block of rows row0 .. row0 + 31 (a0 .. a0 + 31 of one vector)
+  // and columns n0 .. n0 + 31 (b0 .. b0 + 31 of one operator j) is the block of
+  // T' (rows v*kB + b, columns j*kA + a) at x = j*kA + a0, y = v*kB + b0.
+  __device__ bool block_xy(int row0, int n0, int* x, int* y) const {
+    if ((kA & 31) || (kB & 31) || (row0 & 31) || (n0 & 31)) return false;
+    const int v = row0 / kA, a0 = row0 % kA, j = n0 / kB, b0 = n0 % kB;
+    *x = j * kA + a0;
+    *y = v * kB + b0;
+    return true;
+  }
+  __device__ void values(int, int, const float (&val)[32], float (&out)[32]) const {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) out[t] = val[t];
+  }
   // cnt (<= 32) consecutive columns n0 .. n0 + cnt - 1 of row m: the index
   // arithmetic once per run, then (j, b) stepped
   __device__ void run(int m, int n0, const float (&val)[32], int cnt) const {
@@ -112,6 +126,34 @@ struct EpiKron2T {  // m = v*kB + b, n = a
     T y = alpha * (acc + (EA[n] + EB[b]) * x) + beta * x;
     if (gamma != T(0)) y += gamma * Z[idx];
     Y[idx] = y;
+  }
+  // The 32 x 32 block of rows row0 .. row0 + 31 (b0 .. b0 + 31 of one vector)
+  // and columns a0 .. a0 + 31 is the block of Y (rows v*kA + a, columns b) at
+  // x = b0, y = v*kA + a0.
+  __device__ bool block_xy(int row0, int n0, int* x, int* y) const {
+    if ((kA & 31) || (kB & 31) || (row0 & 31) || (n0 & 31)) return false;
+    const int v = row0 / kB, b0 = row0 % kB;
+    *x = b0;
+    *y = v * kA + n0;
+    return true;
+  }
+  // the final values of the 32 columns a = n0 .. n0 + 31 of row (v, b)
+  __device__ void values(int m, int n0, const float (&val)[32], float (&out)[32]) const {
+    const int v = m / kB, b = m % kB;
+    const T eb = __ldg(EB + b);
+    const long idx0 = ((long)v * kA + n0) * kB + b;
+    T x[32], z[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      x[t] = __ldg(X + idx0 + (long)t * kB);
+      z[t] = gamma != T(0) ? __ldg(Z + idx0 + (long)t * kB) : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      T y = alpha * ((T)val[t] + (__ldg(EA + n0 + t) + eb) * x[t]) + beta * x[t];
+      if (gamma != T(0)) y += gamma * z[t];
+      out[t] = (float)y;
+    }
   }
   // cnt (<= 32) consecutive columns a = n0 .. n0 + cnt - 1 of row (v, b).
   // Every input of the run is loaded before the first store, so the loads
@@ -742,8 +784,13 @@ __global__ void sort_pairs_kernel(const double* __restrict__ lam, const double* 
 // With `adaptive` set and G already within 1e-3 of the identity, the kernel
 // instead writes the first-order inverse factor I - F^T (F upper triangular,
 // F_ij = E_ij for i < j, F_ii = E_ii / 2, E = G - I), whose error is O(|E|^2).
+// Threads of a launch: 1024 in FP32; 512 in FP64, where 1024 threads (64
+// registers each) made the double-precision factorisation spill.
+template <typename TC>
+constexpr int cholinv_threads() { return sizeof(TC) == 8 ? 512 : 1024; }
+
 template <typename TC, typename TI, typename TO>
-__global__ void __launch_bounds__(1024) cholinv_kernel(const TI* __restrict__ G, int m, double shift,
+__global__ void __launch_bounds__(cholinv_threads<TC>()) cholinv_kernel(const TI* __restrict__ G, int m, double shift,
                                                        TO* __restrict__ Linv, int* __restrict__ status,
                                                        int adaptive = 0) {
   extern __shared__ unsigned char smem_raw[];

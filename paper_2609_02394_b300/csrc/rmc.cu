@@ -543,7 +543,7 @@ EncodeTiledFn encode_tiled() {
 // box 32 x box_rows, 128-byte swizzle, zero fill out of bounds.  False when
 // the TMA cannot address it (pitch not a multiple of 16 bytes, base not
 // 16-byte aligned).
-bool make_map(CUtensorMap* m, const float* ptr, long rows, long K, long ld, int box_rows) {
+bool make_map(CUtensorMap* m, const float* ptr, long rows, long K, long ld, int box_rows, bool swizzle = true) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc || ((uintptr_t)ptr & 15) || (ld % 4) != 0 || K < 1 || rows < 1 || ld < K) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
@@ -551,9 +551,16 @@ bool make_map(CUtensorMap* m, const float* ptr, long rows, long K, long ld, int 
   const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1u, 1u};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// Output of the TMA kernel's block stores: a row-major rows x cols FP32 matrix
+// written in 32 x 32 blocks (no swizzle: the staging block is plain row-major).
+struct TmaOut {
+  float* ptr = nullptr;
+  long rows = 0, cols = 0;
+};
 
 int sm_count() {
   static int n = [] {
@@ -587,24 +594,29 @@ bool tma_fits(long lda, long ldb, int K) { return encode_tiled() && K >= 1 && ld
 
 template <class Epi>
 rmc_status launch_tma(rmc_ctx* ctx, const float* A, long lda, int M, const float* B, long ldb, int N, int K,
-                      const Epi& epi, bool* launched) {
+                      const Epi& epi, bool* launched, const TmaOut& out = TmaOut{}) {
   *launched = false;
   int n_tiles, BN;
   tma_n_tiles(N, &n_tiles, &BN);
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mo;
   if (!make_map(&ma, A, M, K, lda, tmag::kBM) || !make_map(&mb, B, N, K, ldb, BN)) return RMC_OK;
-  tmag::Args g{M, N, K, BN, (M + tmag::kBM - 1) / tmag::kBM, n_tiles, ctx->d_status + 3};
+  // block stores when the output can be addressed (otherwise mo is an unused copy)
+  const bool store = out.ptr && make_map(&mo, out.ptr, out.rows, out.cols, out.cols, 32, false);
+  if (!store) mo = mb;
+  tmag::Args g{M, N, K, BN, (M + tmag::kBM - 1) / tmag::kBM, n_tiles, ctx->d_status + 3, store ? 1 : 0};
   const int tiles = g.m_tiles * g.n_tiles;
   const int grid = std::min(tiles, sm_count());
   // the attribute is process-wide: always the largest size any launch needs
   if (tmag::stages_for(BN) == 3) {
     CK(cudaFuncSetAttribute(tmag::gemm_tma_tf32x3_kernel<3, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)tmag::smem_bytes(128, 3)));
-    tmag::gemm_tma_tf32x3_kernel<3, Epi><<<grid, tmag::kThreads, tmag::smem_bytes(BN, 3), ctx->stream>>>(ma, mb, g, epi);
+    tmag::gemm_tma_tf32x3_kernel<3, Epi><<<grid, tmag::kThreads, tmag::smem_bytes(BN, 3), ctx->stream>>>(ma, mb, mo, g,
+                                                                                                   epi);
   } else {
     CK(cudaFuncSetAttribute(tmag::gemm_tma_tf32x3_kernel<2, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)tmag::smem_bytes(256, 2)));
-    tmag::gemm_tma_tf32x3_kernel<2, Epi><<<grid, tmag::kThreads, tmag::smem_bytes(BN, 2), ctx->stream>>>(ma, mb, g, epi);
+    tmag::gemm_tma_tf32x3_kernel<2, Epi><<<grid, tmag::kThreads, tmag::smem_bytes(BN, 2), ctx->stream>>>(ma, mb, mo, g,
+                                                                                                   epi);
   }
   CKL();
   *launched = true;
@@ -620,10 +632,12 @@ rmc_status kron_apply_tc(rmc_ctx* ctx, const KronOp<float>& H, const float* X, i
   // TMA can address its operands, else on the plain-load kernel.
   bool done = false;
   const EpiKron1T<float> e1{Tbuf, kA, kB, no};
-  TRY(launch_tma(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, e1, &done));
+  TRY(launch_tma(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, e1, &done,
+                 TmaOut{Tbuf, (long)nv * kB, (long)no * kA}));
   if (!done) TRY(launch_tc(ctx, X, kB, nv * kA, H.Bcat, kB, no * kB, kB, e1));
   const EpiKron2T<float> e2{X, Z, H.EA, H.EB, Y, kA, kB, alpha, beta, gamma};
-  TRY(launch_tma(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA, e2, &done));
+  TRY(launch_tma(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA, e2, &done,
+                 TmaOut{Y, (long)nv * kA, (long)kB}));
   if (!done) TRY(launch_tc(ctx, Tbuf, (long)no * kA, nv * kB, H.Acat, (long)no * kA, kA, no * kA, e2));
   return RMC_OK;
 }
@@ -888,7 +902,7 @@ rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, dou
   const size_t sm = cholinv_smem_bytes(nv, sizeof(T));
   for (int pass = 0; pass < 2; ++pass) {
     TRY(gram<T>(ctx, ws, X, nv, X, nv, n, G, true));
-    cholinv_kernel<T, T, T><<<1, 1024, sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2,
+    cholinv_kernel<T, T, T><<<1, cholinv_threads<T>(), sm, ctx->stream>>>(G, nv, pass == 0 ? shift : 0.0, Li, ctx->d_status + 2,
                                                           pass == 0 ? 0 : 1);
     CKL();
     TRY(combine<T>(ctx, Li, false, nv, nv, X, n, tmp, T(1), T(0), nullptr));
@@ -915,7 +929,7 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
                             (int)cholinv_smem_bytes(kMaxSmallDim, sizeof(double))));
     for (int pass = 0; pass < 2; ++pass) {
       TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
-      cholinv_kernel<double, double, double><<<1, 1024, sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2, pass);
+      cholinv_kernel<double, double, double><<<1, cholinv_threads<double>(), sm, ctx->stream>>>(G, nv, 0.0, Li, ctx->d_status + 2, pass);
       CKL();
       TRY(combine<double>(ctx, Li, false, nv, nv, X, n, tmp, 1.0, 0.0, nullptr));
       CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -21,10 +21,15 @@
 //              shared memory (same swizzled layout, elementwise), fence them
 //              to the async proxy and arrive on the stage's `conv` barrier;
 //   warps 6-9  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//              lanes 32 (w % 4) .. + 31, i.e. tile rows) and hand each run of
-//              32 consecutive columns of a row to the epilogue functor's
-//              run(m, n0, values, count), then free the accumulator buffer
-//              (`acce`).
+//              lanes 32 (w % 4) .. + 31, i.e. tile rows), then free the
+//              accumulator buffer (`acce`).  Where the functor maps the warp's
+//              32 rows x 32 columns onto a 32 x 32 block of a 2-D output
+//              (block_xy), the final values (values) go transposed into a
+//              shared-memory staging block and out with one TMA tensor store
+//              (two staging blocks a warp, bulk groups waited on before a
+//              block is reused and before exit); otherwise each run of 32
+//              consecutive columns of a row goes to the functor's
+//              run(m, n0, values, count).
 // The accumulator is double-buffered (2 x 256 TMEM columns), so the epilogue of
 // one tile overlaps the MMAs of the next; the K chunks run through a ring of
 // kStages stages (2 for 256-column tiles, 3 for tiles of <= 128 columns, the
@@ -83,13 +88,17 @@ struct Args {
   int BN;        // N tile, multiple of 16, <= 256
   int m_tiles, n_tiles;
   int* err;
+  int tma_store;  // 1: the epilogue writes 32 x 32 output blocks with TMA stores (mapO)
 };
+
+constexpr uint32_t kStageBlock = 32 * 32 * 4;    // one 32 x 32 FP32 output block
+constexpr uint32_t kStoreBytes = 4 * 2 * kStageBlock;  // 4 epilogue warps x 2 buffers
 
 // stages that fit 227 KB of shared memory with the hi and lo tiles of A and B
 __host__ __device__ inline int stages_for(int BN) { return BN <= 128 ? 3 : 2; }
 
 __host__ __device__ inline size_t smem_bytes(int BN, int stages) {
-  return 1024 + (size_t)stages * 2 * (kABytes + (size_t)BN * 128);
+  return 1024 + (size_t)stages * 2 * (kABytes + (size_t)BN * 128) + kStoreBytes;
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -111,6 +120,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 2-D tiled TMA store of a 32 x 32 FP32 block from shared memory (bulk group).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)map),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one bulk group of this thread still reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -131,7 +151,7 @@ __device__ __forceinline__ void lo_tile(const unsigned char* hi, unsigned char* 
 template <int kStages, class Epi>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tma_tf32x3_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                           Args g, Epi epi) {
+                           const __grid_constant__ CUtensorMap mapO, Args g, Epi epi) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], accf[2], acce[2], last;
   __shared__ uint32_t tmem_base;
@@ -268,6 +288,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- epilogue ----
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    // two 32 x 32 staging blocks of this warp for the TMA stores
+    float* stg0 = (float*)(base + (size_t)kStages * stage_bytes + (size_t)(warp - kEpiWarp0) * 2 * kStageBlock);
+    int sbuf = 0;
     int tc = 0;
     for (int t = blockIdx.x; t < tiles && !stopped(); t += gridDim.x, ++tc) {
       const int ab = tc & 1;
@@ -283,12 +306,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u + (uint32_t)cc, v);
         const int cnt = min(32, min(g.BN - cc, g.N - (n0 + cc)));
-        if (row < g.M && cnt > 0) epi.run(row, n0 + cc, v, cnt);
+        int bx = 0, by = 0;
+        const int row0 = mt * kBM + q * 32;
+        if (g.tma_store && cnt == 32 && row0 + 31 < g.M && epi.block_xy(row0, n0 + cc, &bx, &by)) {
+          // the warp's 32 x 32 block: final values, transposed into shared
+          // memory (row r of the block = output column n0 + cc + r, lanes
+          // along the block's inner dimension), one TMA store
+          float o[32];
+          epi.values(row, n0 + cc, v, o);
+          float* stg = stg0 + sbuf * 1024;
+          if (lane == 0) bulk_wait_read_1();  // the store that used this buffer has read it
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < 32; ++r) stg[r * 32 + lane] = o[r];
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&mapO, bx, by, stg);
+            bulk_commit();
+          }
+          sbuf ^= 1;
+        } else if (row < g.M && cnt > 0) {
+          epi.run(row, n0 + cc, v, cnt);
+        }
       }
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[ab]);
     }
+    if (lane == 0) bulk_wait_all();  // every TMA store of this warp has completed
+    __syncwarp();
   }
   fence_before_sync();
   __syncthreads();
