@@ -442,15 +442,31 @@ rmc_status rmc_block_import(rmc_ctx* ctx, int k, const double* E, int n_ops,
  * gamma == 0; Y must not alias X or Z); A: n_ops x kA x kA; B: n_ops x kB x kB;
  * EA[kA], EB[kB], coef[n_ops]: all device pointers of `dtype` (0 = FP64,
  * 1 = FP32 on the FP32 pipe, 2 = FP32 data on the tcgen05 tensor cores in the
- * 3xTF32 form, which needs 1 <= n_ops, n_ops * kB <= 256 and kA <= 256, else
- * RMC_ERR_INVAL; coef, alpha, beta, gamma are always double on the host side
- * and coef is a host array).  The intermediate products are held in scratch
+ * 3xTF32 form, which needs n_ops >= 1 and, for each of the two stages, either
+ * 16-byte row pitches (kB % 4 == 0 for the first, n_ops * kA % 4 == 0 for the
+ * second: the TMA-fed kernel, any size) or at most 256 output columns
+ * (n_ops * kB, resp. kA: the plain-load kernel), else RMC_ERR_INVAL; coef,
+ * alpha, beta, gamma are always double on the host side and coef is a host
+ * array).  The intermediate products are held in scratch
  * memory the library allocates from the context (RMC_ERR_NOMEM if the budget
  * is exceeded).  Runs on the context stream; does not synchronise. */
 rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv,
                            const void* EA, const void* EB, const void* A, const void* B,
                            const double* coef, const void* X, void* Y, const void* Z,
                            double alpha, double beta, double gamma);
+
+/* Gram product of two vector blocks (the orthogonalisation and Rayleigh-Ritz
+ * contractions of the subspace iteration):
+ *   G[i][j] = <X1[i], X2[j]>  (G: nv1 x nv2, row-major; X1: nv1 x n, X2: nv2 x n,
+ *                              vector-major, all device FP32),
+ * symmetrised ((G + G^T) / 2) when symmetrize != 0 and nv1 == nv2.  dtype 1:
+ * the FP32 pipe (split-K SIMT GEMM); dtype 2: the tcgen05 tensor cores in the
+ * 3xTF32 form, split-K over the TMA-fed kernel (needs n % 4 == 0 and 16-byte
+ * aligned blocks, else RMC_ERR_INVAL).  Partial products of the splits go to
+ * library scratch (RMC_ERR_NOMEM beyond the budget) and are summed in a fixed
+ * order.  Runs on the context stream; does not synchronise. */
+rmc_status rmc_gram(rmc_ctx* ctx, int dtype, int nv1, int nv2, long n, const float* X1, const float* X2,
+                    float* G, int symmetrize);
 
 /* The Chebyshev filter of one subspace iteration (Zhou and Saad's scaled
  * three-term recurrence on the H_eff of Eq. (7), the operator arguments as in

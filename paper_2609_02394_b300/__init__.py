@@ -33,7 +33,7 @@ EXPORTED = [
     "rmc_create", "rmc_destroy", "rmc_last_error", "rmc_mem_in_use", "rmc_stats", "rmc_stream",
     "rmc_build_leaf", "rmc_build_leaf_pauli", "rmc_couple", "rmc_lowest", "rmc_solve_chain",
     "rmc_block_free", "rmc_block_info", "rmc_block_export", "rmc_block_import",
-    "rmc_kron_matvec", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
+    "rmc_kron_matvec", "rmc_gram", "rmc_syev", "rmc_rotate_op", "rmc_profile", "rmc_profile_read",
     "rmc_kron_matvec_noalloc", "rmc_server_create", "rmc_server_destroy", "rmc_submit", "rmc_poll",
     "rmc_server_stats", "rmc_estimate_bytes", "rmc_solve_chains", "rmc_server_profile",
     "rmc_server_profile_read", "rmc_server_last_error", "rmc_cheb_filter", "rmc_solve_chain_states",
@@ -135,6 +135,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rmc_block_export": ([vp, vp, P(dp), P(dp), P(dp)], ip),
         "rmc_block_import": ([vp, ip, P(dp), ip, P(dp), P(rmc_op_tag), ip, P(dp), P(vp)], ip),
         "rmc_kron_matvec": ([vp, ip, ip, ip, ip, ip, vp, vp, vp, vp, P(dp), vp, vp, vp, dp, dp, dp], ip),
+        "rmc_gram": ([vp, ip, ip, ip, ctypes.c_long, vp, vp, vp, ip], ip),
         "rmc_syev": ([vp, ip, vp, vp, vp], ip),
         "rmc_rotate_op": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
         "rmc_profile": ([vp, ip], ip),
@@ -480,6 +481,10 @@ class Context:
         c = _f64(coef if len(coef) else [0.0])
         self._check(self.lib.rmc_kron_matvec(self.h, dtype, kA, kB, n_ops, nv, EA, EB, A or None, B or None,
                                              _dptr(c), X, Y, Z or None, alpha, beta, gamma))
+
+    def gram(self, dtype: int, nv1: int, nv2: int, n: int, X1: int, X2: int, G: int, symmetrize: bool = False):
+        """G = X1 X2^T (device FP32 pointers); dtype 1 FP32 pipe, 2 tensor cores."""
+        self._check(self.lib.rmc_gram(self.h, dtype, nv1, nv2, n, X1, X2, G, 1 if symmetrize else 0))
 
     def cheb_filter(self, dtype: int, kA: int, kB: int, n_ops: int, nv: int, EA: int, EB: int, A: int, B: int,
                     coef, X: int, deg: int, theta0: float, a: float, ub: float, fused: bool, Y: int):

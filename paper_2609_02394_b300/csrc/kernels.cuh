@@ -79,20 +79,20 @@ struct EpiKron1T {  // m = v*kA + a, n = j*kB + b  ->  T'[(v*kB + b)*(n_ops*kA) 
   // The 32 x 32 block of rows row0 .. row0 + 31 (a0 .. a0 + 31 of one vector)
   // and columns n0 .. n0 + 31 (b0 .. b0 + 31 of one operator j) is the block of
   // T' (rows v*kB + b, columns j*kA + a) at x = j*kA + a0, y = v*kB + b0.
-  __device__ bool block_xy(int row0, int n0, int* x, int* y) const {
+  __device__ bool block_xy(int, int row0, int n0, int* x, int* y) const {
     if ((kA & 31) || (kB & 31) || (row0 & 31) || (n0 & 31)) return false;
     const int v = row0 / kA, a0 = row0 % kA, j = n0 / kB, b0 = n0 % kB;
     *x = j * kA + a0;
     *y = v * kB + b0;
     return true;
   }
-  __device__ void values(int, int, const float (&val)[32], float (&out)[32]) const {
+  __device__ void values(int, int, int, const float (&val)[32], float (&out)[32]) const {
 #pragma unroll
     for (int t = 0; t < 32; ++t) out[t] = val[t];
   }
   // cnt (<= 32) consecutive columns n0 .. n0 + cnt - 1 of row m: the index
   // arithmetic once per run, then (j, b) stepped
-  __device__ void run(int m, int n0, const float (&val)[32], int cnt) const {
+  __device__ void run(int, int m, int n0, const float (&val)[32], int cnt) const {
     const int v = m / kA, a = m % kA;
     int j = n0 / kB, b = n0 % kB;
     const long ld = (long)n_ops * kA;
@@ -130,7 +130,7 @@ struct EpiKron2T {  // m = v*kB + b, n = a
   // The 32 x 32 block of rows row0 .. row0 + 31 (b0 .. b0 + 31 of one vector)
   // and columns a0 .. a0 + 31 is the block of Y (rows v*kA + a, columns b) at
   // x = b0, y = v*kA + a0.
-  __device__ bool block_xy(int row0, int n0, int* x, int* y) const {
+  __device__ bool block_xy(int, int row0, int n0, int* x, int* y) const {
     if ((kA & 31) || (kB & 31) || (row0 & 31) || (n0 & 31)) return false;
     const int v = row0 / kB, b0 = row0 % kB;
     *x = b0;
@@ -138,7 +138,7 @@ struct EpiKron2T {  // m = v*kB + b, n = a
     return true;
   }
   // the final values of the 32 columns a = n0 .. n0 + 31 of row (v, b)
-  __device__ void values(int m, int n0, const float (&val)[32], float (&out)[32]) const {
+  __device__ void values(int, int m, int n0, const float (&val)[32], float (&out)[32]) const {
     const int v = m / kB, b = m % kB;
     const T eb = __ldg(EB + b);
     const long idx0 = ((long)v * kA + n0) * kB + b;
@@ -159,7 +159,7 @@ struct EpiKron2T {  // m = v*kB + b, n = a
   // Every input of the run is loaded before the first store, so the loads
   // overlap (a store to Y could otherwise alias a later X load and serialise
   // them on the memory latency).
-  __device__ void run(int m, int n0, const float (&val)[32], int cnt) const {
+  __device__ void run(int, int m, int n0, const float (&val)[32], int cnt) const {
     const int v = m / kB, b = m % kB;
     const T eb = __ldg(EB + b);
     const long idx0 = ((long)v * kA + n0) * kB + b;
@@ -179,6 +179,54 @@ struct EpiKron2T {  // m = v*kB + b, n = a
     }
   }
 };
+
+// Split-K partial products of the tensor-core Gram form, stored transposed:
+// split sp of acc[m][n] to Pt[(sp*N + n)*M + m] (Pt viewed as a (splits*N) x M
+// row-major matrix, so a warp's 32 rows m are the inner dimension of its
+// 32 x 32 TMA block store, as the staging layout has them).
+struct EpiSplitT {
+  float* Pt;
+  int M, N;
+  __device__ bool block_xy(int sp, int row0, int n0, int* x, int* y) const {
+    *x = row0;
+    *y = sp * N + n0;
+    return true;
+  }
+  __device__ void values(int, int, int, const float (&val)[32], float (&out)[32]) const {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) out[t] = val[t];
+  }
+  __device__ void run(int sp, int m, int n0, const float (&val)[32], int cnt) const {
+    float* p = Pt + ((long)sp * N + n0) * M + m;
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (t < cnt) p[(long)t * M] = val[t];
+  }
+};
+
+// G[m][n] = sum over the splits of Pt[(sp*N + n)*M + m], in split order
+// (consecutive threads take consecutive m, so the reads of Pt are coalesced).
+__global__ void reduce_splits_t_kernel(const float* __restrict__ Pt, int splits, int M, int N, float* __restrict__ G) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int n = (int)(e / M), m = (int)(e % M);
+    float acc = 0.0f;
+    for (int sp = 0; sp < splits; ++sp) acc += Pt[sp * total + e];
+    G[(long)m * N + n] = acc;
+  }
+}
+
+// G <- (G + G^T) / 2 for a square m x m matrix (each pair once).
+__global__ void symmetrize_kernel(float* __restrict__ G, int m) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)m * m; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    if (j > i) {
+      const float v = 0.5f * (G[(long)i * m + j] + G[(long)j * m + i]);
+      G[(long)i * m + j] = v;
+      G[(long)j * m + i] = v;
+    }
+  }
+}
 
 // Y = alpha * acc + beta * Src (Src may alias nothing written by the GEMM).
 template <typename T>

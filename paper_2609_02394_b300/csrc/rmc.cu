@@ -354,10 +354,31 @@ void gemm_tile(int tile, const T* A, const T* B, const GemmShape& s, int batches
 // G (nv1 x nv2) = X1 X2^T, contraction over n, deterministic split-K.
 // Candidates: tile in {64, 48, 32} x split-K in {s, s/2, 2s}, s the default
 // split count (about two CTA waves of the 64 x 64 tiling, >= 128 terms a split).
+// Tensor-core Gram products (FP32 data, 3xTF32) for the long contractions of
+// the wide merges (n >= kTcGramMinN): split-K over about two waves of CTAs,
+// partial 128 x BN tiles to P, then the deterministic split reduction.
+constexpr long kTcGramMinN = 16384;
+
+bool tc_gram(const rmc_ctx* ctx, const float* X1, const float* X2, long n);
+rmc_status gram_tc(rmc_ctx* ctx, Workspace& ws, const float* X1, int nv1, const float* X2, int nv2, long n, float* G,
+                   bool symmetrize);
+
+// tensor_ok: the caller accepts 3xTF32 accuracy (~5e-7 relative a product,
+// against ~6e-8 for FP32), e.g. projections whose coefficients are applied
+// again, or Gram products of small corrections; Gram matrices that are
+// factorised (Cholesky-QR of a filtered block, conditioned up to ~1e6: 3xTF32
+// made the factorisation fail) or diagonalised must stay on the FP32 pipe.  No
+// solver call sets it: at the 256-state merges' shapes (M, N <= 288,
+// K = 65536) the split-K tensor-core form measured 2.6 ms against 0.14-0.57 ms
+// on the FP32 pipe (each of its TMA boxes reads 128 bytes from each of up to
+// 288 rows 256 KB apart, from 148 CTAs at once); rmc_gram exposes both forms.
 template <typename T>
 rmc_status gram(rmc_ctx* ctx, Workspace& ws, const T* X1, int nv1, const T* X2, int nv2, long n, T* G,
-                bool symmetrize) {
+                bool symmetrize, bool tensor_ok = false) {
   ProfScope ps(ctx, 4, 2.0 * nv1 * nv2 * (double)n);
+  if constexpr (sizeof(T) == 4) {
+    if (tensor_ok && tc_gram(ctx, X1, X2, n)) return gram_tc(ctx, ws, X1, nv1, X2, nv2, n, G, symmetrize);
+  }
   bool df = false;
   if constexpr (sizeof(T) == 8) df = fp64_by_df(ctx);
   const int tiles64 = (int)(ceil_div(nv1, 64) * ceil_div(nv2, 64));
@@ -584,7 +605,7 @@ int tma_max_bn() {
   return v;
 }
 
-inline void tma_n_tiles(int N, int* n_tiles, int* BN) {
+void tma_n_tiles(int N, int* n_tiles, int* BN) {
   const int mx = tma_max_bn();
   *n_tiles = (N + mx - 1) / mx;
   *BN = ((N + *n_tiles - 1) / *n_tiles + 15) / 16 * 16;
@@ -594,7 +615,8 @@ bool tma_fits(long lda, long ldb, int K) { return encode_tiled() && K >= 1 && ld
 
 template <class Epi>
 rmc_status launch_tma(rmc_ctx* ctx, const float* A, long lda, int M, const float* B, long ldb, int N, int K,
-                      const Epi& epi, bool* launched, const TmaOut& out = TmaOut{}) {
+                      const Epi& epi, bool* launched, const TmaOut& out = TmaOut{}, int k_splits = 1,
+                      int kc_split = 0) {
   *launched = false;
   int n_tiles, BN;
   tma_n_tiles(N, &n_tiles, &BN);
@@ -603,7 +625,9 @@ rmc_status launch_tma(rmc_ctx* ctx, const float* A, long lda, int M, const float
   // block stores when the output can be addressed (otherwise mo is an unused copy)
   const bool store = out.ptr && make_map(&mo, out.ptr, out.rows, out.cols, out.cols, 32, false);
   if (!store) mo = mb;
-  tmag::Args g{M, N, K, BN, (M + tmag::kBM - 1) / tmag::kBM, n_tiles, ctx->d_status + 3, store ? 1 : 0};
+  const int kcs = (K + 31) / 32;
+  tmag::Args g{M, N, K, BN, (M + tmag::kBM - 1) / tmag::kBM, n_tiles, ctx->d_status + 3, store ? 1 : 0,
+               std::max(1, k_splits), kc_split > 0 ? kc_split : kcs};
   const int tiles = g.m_tiles * g.n_tiles;
   const int grid = std::min(tiles, sm_count());
   // the attribute is process-wide: always the largest size any launch needs
@@ -620,6 +644,35 @@ rmc_status launch_tma(rmc_ctx* ctx, const float* A, long lda, int M, const float
   }
   CKL();
   *launched = true;
+  return RMC_OK;
+}
+
+bool tc_gram(const rmc_ctx* ctx, const float* X1, const float* X2, long n) {
+  return ctx->cfg.precision != RMC_PREC_FP64 && n >= kTcGramMinN && n % 4 == 0 && !((uintptr_t)X1 & 15) &&
+         !((uintptr_t)X2 & 15) && encode_tiled();
+}
+
+rmc_status gram_tc(rmc_ctx* ctx, Workspace& ws, const float* X1, int nv1, const float* X2, int nv2, long n, float* G,
+                   bool symmetrize) {
+  const int kcs = (int)((n + 31) / 32);
+  int n_tiles, BN;
+  tma_n_tiles(nv2, &n_tiles, &BN);
+  const int mn = (nv1 + tmag::kBM - 1) / tmag::kBM * n_tiles;
+  int ks = std::max(1, std::min(kcs, (2 * sm_count() + mn - 1) / mn));
+  const int kc_split = (kcs + ks - 1) / ks;
+  ks = (kcs + kc_split - 1) / kc_split;
+  float* P = nullptr;
+  TRY(ws.get(&P, (size_t)ks * nv1 * nv2));
+  bool done = false;
+  TRY(launch_tma(ctx, X1, n, nv1, X2, n, nv2, (int)n, EpiSplitT{P, nv1, nv2}, &done,
+                 TmaOut{P, (long)ks * nv2, (long)nv1}, ks, kc_split));
+  if (!done) return fail(ctx, RMC_ERR_INVAL, "tensor-core Gram product: operands not addressable by the TMA");
+  reduce_splits_t_kernel<<<grid1d((long)nv1 * nv2), 256, 0, ctx->stream>>>(P, ks, nv1, nv2, G);
+  CKL();
+  if (symmetrize && nv1 == nv2) {
+    symmetrize_kernel<<<grid1d((long)nv1 * nv1), 256, 0, ctx->stream>>>(G, nv1);
+    CKL();
+  }
   return RMC_OK;
 }
 
@@ -2455,6 +2508,21 @@ rmc_status rmc_kron_matvec(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, i
     return kron_apply<T>(ctx, H, (const T*)X, nv, (T*)Y, (T)alpha, (T)beta, (T)gamma, (const T*)Z, Tbuf);
   };
   return dtype == 0 ? run(double{}) : run(float{});
+}
+
+rmc_status rmc_gram(rmc_ctx* ctx, int dtype, int nv1, int nv2, long n, const float* X1, const float* X2, float* G,
+                    int symmetrize) {
+  TRY(check_ctx(ctx));
+  if (nv1 < 1 || nv2 < 1 || n < 1 || !X1 || !X2 || !G || (dtype != 1 && dtype != 2) ||
+      (symmetrize && nv1 != nv2))
+    return fail(ctx, RMC_ERR_INVAL, "rmc_gram: bad arguments");
+  Workspace ws(ctx);
+  if (dtype == 2) {
+    if (n % 4 != 0 || ((uintptr_t)X1 & 15) || ((uintptr_t)X2 & 15) || !encode_tiled())
+      return fail(ctx, RMC_ERR_INVAL, "rmc_gram: the tensor-core form needs n %% 4 == 0 and 16-byte aligned blocks");
+    return gram_tc(ctx, ws, X1, nv1, X2, nv2, n, G, symmetrize != 0);
+  }
+  return gram<float>(ctx, ws, X1, nv1, X2, nv2, n, G, symmetrize != 0, false);
 }
 
 rmc_status rmc_cheb_filter(rmc_ctx* ctx, int dtype, int kA, int kB, int n_ops, int nv, const void* EA,

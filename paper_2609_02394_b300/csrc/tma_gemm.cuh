@@ -89,6 +89,8 @@ struct Args {
   int m_tiles, n_tiles;
   int* err;
   int tma_store;  // 1: the epilogue writes 32 x 32 output blocks with TMA stores (mapO)
+  int k_splits;   // K split into k_splits ranges of kc_split 32-wide chunks (split-K);
+  int kc_split;   // each (tile, split) accumulates one range and hands the split index on
 };
 
 constexpr uint32_t kStageBlock = 32 * 32 * 4;    // one 32 x 32 FP32 output block
@@ -160,8 +162,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t b_bytes = (uint32_t)g.BN * 128;
   const uint32_t stage_bytes = 2 * (kABytes + b_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles = g.m_tiles * g.n_tiles;
-  const int kcs = (g.K + 31) / 32;
+  const int tiles = g.m_tiles * g.n_tiles * g.k_splits;
+  const int kcs_all = (g.K + 31) / 32;
+  // work item t: output tile (mt, nt) and K range ks (chunks kc0 .. kc0 + count - 1)
+  auto decode = [&](int t, int* mt, int* nt, int* ks, int* kc0, int* count) {
+    const int mn = t / g.k_splits;
+    *ks = t % g.k_splits;
+    *mt = mn / g.n_tiles;
+    *nt = mn % g.n_tiles;
+    *kc0 = *ks * g.kc_split;
+    *count = max(0, min(kcs_all - *kc0, g.kc_split));
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -197,7 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int it = 0;
       for (int t = blockIdx.x; t < tiles && !stopped(); t += gridDim.x) {
-        const int mt = t / g.n_tiles, nt = t % g.n_tiles;
+        int mt, nt, ks, kc0, kcs;
+        decode(t, &mt, &nt, &ks, &kc0, &kcs);
         for (int kc = 0; kc < kcs; ++kc, ++it) {
           const int s = it % kStages;
           const uint32_t ph = (uint32_t)(it / kStages) & 1u;
@@ -207,8 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           unsigned char* st = base + (size_t)s * stage_bytes;
           mbar_arrive_expect_tx(&full[s], kABytes + b_bytes);
-          tma_load_2d(st, &mapA, kc * 32, mt * kBM, &full[s]);
-          tma_load_2d(st + kABytes, &mapB, kc * 32, nt * g.BN, &full[s]);
+          tma_load_2d(st, &mapA, (kc0 + kc) * 32, mt * kBM, &full[s]);
+          tma_load_2d(st + kABytes, &mapB, (kc0 + kc) * 32, nt * g.BN, &full[s]);
         }
       }
       // the last loads of every stage have landed before the CTA may exit
@@ -223,6 +235,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_tf32(kBM, g.BN);
       int it = 0, tc = 0;
       for (int t = blockIdx.x; t < tiles && !stopped(); t += gridDim.x, ++tc) {
+        int mt, nt, ks, kc0, kcs;
+        decode(t, &mt, &nt, &ks, &kc0, &kcs);
         const int ab = tc & 1;
         if (!mbar_wait(&acce[ab], ((uint32_t)(tc >> 1) & 1u) ^ 1u, kSpin)) {
           give_up();
@@ -266,6 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ct = threadIdx.x - kConvWarp0 * 32;
     int it = 0;
     for (int t = blockIdx.x; t < tiles && !stopped(); t += gridDim.x) {
+      int mt, nt, ks, kc0, kcs;
+      decode(t, &mt, &nt, &ks, &kc0, &kcs);
       bool ok = true;
       for (int kc = 0; kc < kcs; ++kc, ++it) {
         const int s = it % kStages;
@@ -299,7 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       fence_after_sync();
-      const int mt = t / g.n_tiles, nt = t % g.n_tiles;
+      int mt, nt, ks, kc0, kcs;
+      decode(t, &mt, &nt, &ks, &kc0, &kcs);
       const int row = mt * kBM + q * 32 + lane;
       const int n0 = nt * g.BN;
       for (int cc = 0; cc < g.BN; cc += 32) {
@@ -308,12 +325,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cnt = min(32, min(g.BN - cc, g.N - (n0 + cc)));
         int bx = 0, by = 0;
         const int row0 = mt * kBM + q * 32;
-        if (g.tma_store && cnt == 32 && row0 + 31 < g.M && epi.block_xy(row0, n0 + cc, &bx, &by)) {
+        if (g.tma_store && cnt == 32 && row0 + 31 < g.M && epi.block_xy(ks, row0, n0 + cc, &bx, &by)) {
           // the warp's 32 x 32 block: final values, transposed into shared
           // memory (row r of the block = output column n0 + cc + r, lanes
           // along the block's inner dimension), one TMA store
           float o[32];
-          epi.values(row, n0 + cc, v, o);
+          epi.values(ks, row, n0 + cc, v, o);
           float* stg = stg0 + sbuf * 1024;
           if (lane == 0) bulk_wait_read_1();  // the store that used this buffer has read it
           __syncwarp();
@@ -327,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           sbuf ^= 1;
         } else if (row < g.M && cnt > 0) {
-          epi.run(row, n0 + cc, v, cnt);
+          epi.run(ks, row, n0 + cc, v, cnt);
         }
       }
       fence_before_sync();

@@ -76,6 +76,32 @@ def test_wide_kron_matvec_matches_kronecker_form(ctx, kA, kB, n_ops, nv, dtype):
         assert np.abs(got - ref).max() <= 3e-5 * scale, (alpha, beta, gamma, np.abs(got - ref).max() / scale)
 
 
+@pytest.mark.parametrize("nv1,nv2,n,sym", [(160, 160, 65536, True), (128, 160, 65536, False), (288, 288, 16384, True),
+                                          (37, 200, 4096, False), (5, 7, 1000, False), (96, 96, 4100, True)])
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_gram_matches_numpy(ctx, nv1, nv2, n, sym, dtype):
+    """G = X1 X2^T over long contractions (the Gram products of the wide
+    merges: split-K over many CTAs, ragged M and N tiles, the split partial
+    sums reduced in a fixed order) against an FP64 product; FP32 and 3xTF32
+    both within 2e-5 of max |G| (contractions of up to 65536 terms)."""
+    if dtype == 2 and n % 4:
+        pytest.skip("the tensor-core form needs n % 4 == 0")
+    rng = np.random.default_rng(nv1 * 7 + nv2 * 13 + n + dtype)
+    X1 = rng.standard_normal((nv1, n)) / np.sqrt(n)
+    X2 = X1.copy() if sym else rng.standard_normal((nv2, n)) / np.sqrt(n)
+    ref = X1 @ X2.T
+    if sym:
+        ref = 0.5 * (ref + ref.T)
+    d1, d2 = dev(X1, np.float32), dev(X2, np.float32)
+    G = dev(np.full((nv1, nv2), np.nan), np.float32)
+    torch_cuda().cuda.synchronize()
+    ctx.gram(dtype, nv1, nv2, n, d1.data_ptr(), d2.data_ptr(), G.data_ptr(), sym)
+    got = host(G)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= 2e-5 * scale, np.abs(got - ref).max() / scale
+
+
 def _dense_reference(EA, EB, oA, oB, coef, X, alpha, beta, gamma, Z):
     H = O.effective_hamiltonian(EA, EB, [(coef[j], oA[j], oB[j]) for j in range(len(coef))])
     nv, kA, kB = X.shape
