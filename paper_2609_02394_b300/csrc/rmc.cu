@@ -988,7 +988,10 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
       CK(cudaMemcpyAsync(X, tmp, sizeof(double) * nv * n, cudaMemcpyDeviceToDevice, ctx->stream));
     }
   }
-  for (int pass = 0; pass < (wide ? 3 : 2); ++pass) {
+  // first-order passes square the deviation from orthonormality: two take a
+  // block within 1e-3 of orthonormal (a wide block here comes from the FP32
+  // phase, ~1e-6, or from the refinement, ~1e-11) to rounding level
+  for (int pass = 0; pass < 2; ++pass) {
     TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
     cholqr_first_order_kernel<<<grid1d((long)nv * nv), 256, 0, ctx->stream>>>(G, nv, Li);
     CKL();
@@ -2006,8 +2009,12 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
   TRY(new_block(ctx, keff, nc, (int)n, &blk));
   CK(cudaMemcpyAsync(blk->E, w, sizeof(double) * keff, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaMemcpyAsync(blk->basis, C, sizeof(double) * keff * n, cudaMemcpyDeviceToDevice, ctx->stream));
-  // rotate carried operators: out = C^T (o (x) I) C or C^T (I (x) o) C
+  // rotate carried operators: out = C^T (o (x) I) C or C^T (I (x) o) C; the
+  // mixed paths form T = (o (x) I) C in double-FP32 like their other
+  // FP64-accurate block products (the part's DFMA rate is ~1/4 of that)
   double* Tr = Tb64;
+  const bool rot_df = fp64_by_df(ctx);
+  ProfScope ps_rot(ctx, 6, 0.0);
   for (int j = 0; j < nc; ++j) {
     const rmc_carry& cr = in.carry[j];
     const rmc_block* src = cr.side == 0 ? A : B;
@@ -2015,11 +2022,13 @@ rmc_status couple_impl(rmc_ctx* ctx, const MergeInput& in, rmc_block** out, rmc_
     if (cr.side == 0) {
       GemmShape s{kA, kB, kA, kA, kB, 0, n, 1};
       EpiAxpby<double> e{Tr, nullptr, kB, 0, n, 0, 1.0, 0.0};
-      gemm_big<double, false, false>(o, blk->basis, s, keff, e, ctx->stream);
+      if (rot_df) gemm_df<false, false>(o, blk->basis, s, keff, e, ctx->stream);
+      else gemm_big<double, false, false>(o, blk->basis, s, keff, e, ctx->stream);
     } else {
       GemmShape s{keff * kA, kB, kB, kB, kB, 0, 0, 1};
       EpiAxpby<double> e{Tr, nullptr, kB, 0, 0, 0, 1.0, 0.0};
-      gemm_big<double, false, true>(blk->basis, o, s, 1, e, ctx->stream);
+      if (rot_df) gemm_df<false, true>(blk->basis, o, s, 1, e, ctx->stream);
+      else gemm_big<double, false, true>(blk->basis, o, s, 1, e, ctx->stream);
     }
     CKL();
     TRY(gram<double>(ctx, ws, blk->basis, keff, Tr, keff, n, blk->ops + (size_t)j * keff * keff, false));
