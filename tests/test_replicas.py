@@ -22,10 +22,10 @@ def _rank_main(rank, world, port, q):
     import bench
     import torch
     w, r, local, pg = bench.dist_setup()
-    seeds = bench.batch_seeds(r, 4, list(range(100, 108)))
+    seeds = bench.rf_seeds(r, 4)
     pg.barrier()
-    mx = bench.reduce_max(pg, float(10 * (r + 1)), torch.device("cpu"))
-    sm = bench.reduce_sum(pg, float(r + 1), torch.device("cpu"))
+    mx = bench.reduce_op(pg, float(10 * (r + 1)), torch.device("cpu"), "max")
+    sm = bench.reduce_op(pg, float(r + 1), torch.device("cpu"), "sum")
     q.put((r, w, seeds, mx, sm))
     pg.destroy_process_group()
 
@@ -44,12 +44,19 @@ def test_two_rank_replicas_shard_and_reduce():
     (r0, w0, s0, mx0, sm0), (r1, w1, s1, mx1, sm1) = out
     assert (w0, w1) == (2, 2)
     assert set(s0).isdisjoint(s1) and len(s0) == len(s1) == 4
-    assert s0 == [100, 101, 102, 103] and s1 == [104, 105, 106, 107]
+    base = 2609 * 100 + 4
+    assert s0 == [base + 7919 * i for i in range(4)] and s1 == [base + 7919 * i for i in range(4, 8)]
     assert mx0 == mx1 == 20.0
     assert sm0 == sm1 == 3.0
 
 
-def test_seeds_beyond_the_stored_batch_are_fresh():
+def test_every_rank_of_the_xxz_batch_has_stored_oracle_energies():
+    """Replicas of the XXZ batch take instances from the stored oracle set
+    (wrapping around it), so every rank's solves can be validated: a rank past
+    the stored set must not get seeds without a reference."""
     import bench
-    s = bench.batch_seeds(1, 4, [1, 2, 3])
-    assert len(set(s)) == 4 and not set(s) & {1, 2, 3}
+    gold = bench.load_gold_xxz()
+    for rank in range(8):
+        seeds = bench.xxz_seeds(rank, 32, gold.keys())
+        assert len(seeds) == 32 and all(s in gold for s in seeds)
+    assert bench.xxz_seeds(0, 32, gold.keys()) == sorted(gold)[:32]
