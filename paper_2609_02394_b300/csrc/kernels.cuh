@@ -501,16 +501,20 @@ __global__ void gauge_kernel(double* __restrict__ C, long n) {
 }
 
 // ---------------------------------------------------------------------------
-// Small dense symmetric eigensolver, one CTA of 1024 threads: cyclic parallel
-// Jacobi in FP32 with round-robin pairing (all m(m-1)/2 pairs once per sweep,
-// m/2 disjoint rotations per round; each 2x2 block of A updated by one thread
-// as J_k^T A_kl J_l, warps over block rows and lanes over block columns so the
-// inner loops need no integer division).  Stops when the off-diagonal norm is
-// below 1e-6 ||A||_F, or when a sweep no longer halves it (the FP32 rounding
-// floor).  Eigenvalues ascending into w, eigenvectors as columns of the
-// row-major m x m V.  m <= kMaxSmallDim.  status[0] += 1 if the sweep cap was
-// hit first.
+// Small dense symmetric eigensolver, one CTA: cyclic parallel Jacobi in FP32
+// with round-robin pairing (all m(m-1)/2 pairs once per sweep, m/2 disjoint
+// rotations per round; each 2x2 block of A updated as J_k^T A_kl J_l).  Warps
+// take block rows k (and rows of V), lanes take block columns l; a lane keeps
+// the pair and rotation of its columns in registers for the round, so the
+// inner loops do no index arithmetic beyond one multiply-add per access (the
+// kernel is bound by instruction issue on its SM).  Stops when the
+// off-diagonal norm is below 1e-6 ||A||_F, or when a sweep no longer halves it
+// (the FP32 rounding floor).  Eigenvalues ascending into w, eigenvectors as
+// columns of the row-major m x m V.  m <= kMaxSmallDim.  status[0] += 1 if the
+// sweep cap was hit first.
 // ---------------------------------------------------------------------------
+constexpr int kJacobiLaneCols = (kMaxSmallDim / 2 + 31) / 32;  // block columns a lane holds
+
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, int m, TO* __restrict__ w,
                                                       TO* __restrict__ V, int* __restrict__ status, int max_sweeps) {
@@ -577,37 +581,50 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, 
         cs[k] = c; sn[k] = sv; P[k] = p; Q[k] = q;
       }
       __syncthreads();
-      // A <- J^T A J, one 2x2 block per (k, l); the half^2 blocks are dealt
-      // to the threads in order (the launch sizes the CTA so they divide
-      // evenly), lanes of a warp on consecutive l
-      for (int e = tid; e < half * half; e += nt) {
-        const int k = e / half, l = e - k * half;
+      // this lane's block columns l = lane + 32 j
+      int pl[kJacobiLaneCols], ql[kJacobiLaneCols];
+      float cl[kJacobiLaneCols], sl[kJacobiLaneCols];
+#pragma unroll
+      for (int j = 0; j < kJacobiLaneCols; ++j) {
+        const int l = lane + 32 * j;
+        const bool on = l < half;
+        pl[j] = on ? P[l] : 0;
+        ql[j] = on ? Q[l] : 0;
+        cl[j] = on ? cs[l] : 1.f;
+        sl[j] = on ? sn[l] : 0.f;
+      }
+      // A <- J^T A J: block row k on a warp, its block columns on the lanes
+      for (int k = warp; k < half; k += nw) {
         const int pk = P[k], qk = Q[k];
         const float ck = cs[k], sk = sn[k];
-        {
-          const int pl = P[l], ql = Q[l];
-          const float cl = cs[l], sl = sn[l];
-          const float a00 = A[pk * ld + pl], a01 = A[pk * ld + ql];
-          const float a10 = A[qk * ld + pl], a11 = A[qk * ld + ql];
-          const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
-          const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
-          float n00 = b00 * cl - b01 * sl, n01 = b00 * sl + b01 * cl;
-          float n10 = b10 * cl - b11 * sl, n11 = b10 * sl + b11 * cl;
-          if (k == l) { n01 = 0.f; n10 = 0.f; }
-          A[pk * ld + pl] = n00; A[pk * ld + ql] = n01;
-          A[qk * ld + pl] = n10; A[qk * ld + ql] = n11;
+        float* rp = A + pk * ld;
+        float* rq = A + qk * ld;
+#pragma unroll
+        for (int j = 0; j < kJacobiLaneCols; ++j) {
+          const int l = lane + 32 * j;
+          if (l < half) {
+            const float a00 = rp[pl[j]], a01 = rp[ql[j]];
+            const float a10 = rq[pl[j]], a11 = rq[ql[j]];
+            const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
+            const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
+            float n00 = b00 * cl[j] - b01 * sl[j], n01 = b00 * sl[j] + b01 * cl[j];
+            float n10 = b10 * cl[j] - b11 * sl[j], n11 = b10 * sl[j] + b11 * cl[j];
+            if (k == l) { n01 = 0.f; n10 = 0.f; }
+            rp[pl[j]] = n00; rp[ql[j]] = n01;
+            rq[pl[j]] = n10; rq[ql[j]] = n11;
+          }
         }
       }
-      // V <- V J
-      for (int e = tid; e < m * half; e += nt) {
-        const int row = e / half, l = e - row * half;
+      // V <- V J: a row of V on a warp, its column pairs on the lanes
+      for (int row = warp; row < m; row += nw) {
         float* vr = Vs + row * mm;
-        {
-          const int pl = P[l], ql = Q[l];
-          const float c = cs[l], sv = sn[l];
-          const float vp = vr[pl], vq = vr[ql];
-          vr[pl] = c * vp - sv * vq;
-          vr[ql] = sv * vp + c * vq;
+#pragma unroll
+        for (int j = 0; j < kJacobiLaneCols; ++j) {
+          if (lane + 32 * j < half) {
+            const float vp = vr[pl[j]], vq = vr[ql[j]];
+            vr[pl[j]] = cl[j] * vp - sl[j] * vq;
+            vr[ql[j]] = sl[j] * vp + cl[j] * vq;
+          }
         }
       }
       __syncthreads();
@@ -627,15 +644,11 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const TI* __restrict__ S, 
   }
 }
 
-// Threads for jacobi_kernel on an m x m matrix: the fewest multiples of 32
-// (at most 1024) that give every thread the same number of the (m/2)^2 block
-// updates of a round, up to one.
+// Threads for jacobi_kernel on an m x m matrix: a warp for each of the m/2
+// block rows, at least 2 and at most 32 warps.
 inline int jacobi_threads(int m) {
   const int half = ((m + 1) & ~1) / 2;
-  const int blocks = std::max(1, half * half);
-  const int per = (blocks + 1023) / 1024;
-  const int nt = (blocks + per - 1) / per;
-  return std::min(1024, std::max(64, (nt + 31) / 32 * 32));
+  return 32 * std::min(32, std::max(2, half));
 }
 
 inline size_t jacobi_smem_bytes(int m) {
@@ -649,45 +662,91 @@ inline size_t jacobi_smem_bytes(int m) {
 // E_ij = (Sp_ij + lambda_j R_ij) / (lambda_j - lambda_i) where
 // |lambda_i - lambda_j| > delta and R_ij / 2 otherwise (clustered pairs are
 // only re-orthogonalised), delta = 2 (||Sp - diag(lambda)||_F + ||A||_F ||R||_F).
-// One CTA.  R is overwritten by E.
-__global__ void oa_correction_kernel(double* __restrict__ R, const double* __restrict__ Sp,
-                                     const double* __restrict__ A, int m, double* __restrict__ lam,
-                                     int* __restrict__ done, double* __restrict__ prev_emax) {
+// R is overwritten by E.  Three launches, rows of the m x m matrices dealt to
+// the CTAs (an FP64 division per entry: one SM's FP64 rate made a one-CTA
+// form the slowest kernel of the refinement): oa_sums_kernel (lambda and
+// per-CTA partial sums of the three norms), oa_update_kernel (every CTA
+// reduces the partial sums in the same fixed order, then corrects its rows
+// and records its max |E|), oa_finish_kernel (the stop test).  Each returns
+// at once when *done is set.
+__global__ void oa_sums_kernel(const double* __restrict__ R, const double* __restrict__ Sp,
+                               const double* __restrict__ A, int m, double* __restrict__ lam,
+                               double* __restrict__ part, const int* __restrict__ done) {
   if (*done) return;
   __shared__ double red[32];
-  extern __shared__ double sl[];  // m
-  const int tid = threadIdx.x;
-  double an = 0.0;
-  for (int e = tid; e < m * m; e += blockDim.x) an += A[e] * A[e];
-  const double Anorm = sqrt(block_sum(an, red));
-  for (int i = tid; i < m; i += blockDim.x) sl[i] = Sp[i * m + i] / (1.0 - R[i * m + i]);
-  __syncthreads();
-  double off = 0.0, rr = 0.0;
-  for (int e = tid; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e % m;
-    const double d = Sp[e] - (i == j ? sl[i] : 0.0);
-    off += d * d;
-    rr += R[e] * R[e];
+  double an = 0.0, off = 0.0, rr = 0.0;
+  for (int i = blockIdx.x; i < m; i += gridDim.x) {
+    const double* Ai = A + (size_t)i * m;
+    const double* Si = Sp + (size_t)i * m;
+    const double* Ri = R + (size_t)i * m;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double r = Ri[j];
+      double d = Si[j];
+      if (j == i) {
+        const double li = Si[j] / (1.0 - r);
+        lam[i] = li;
+        d -= li;
+      }
+      an += Ai[j] * Ai[j];
+      off += d * d;
+      rr += r * r;
+    }
   }
+  an = block_sum(an, red);
   off = block_sum(off, red);
   rr = block_sum(rr, red);
-  const double delta = 2.0 * (sqrt(off) + Anorm * sqrt(rr));
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = an;
+    part[3 * blockIdx.x + 1] = off;
+    part[3 * blockIdx.x + 2] = rr;
+  }
+}
+
+__global__ void oa_update_kernel(double* __restrict__ R, const double* __restrict__ Sp,
+                                 const double* __restrict__ lam, int m, const double* __restrict__ part, int nparts,
+                                 double* __restrict__ emax_part, const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[32];
+  double an = 0.0, off = 0.0, rr = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    an += part[3 * b];
+    off += part[3 * b + 1];
+    rr += part[3 * b + 2];
+  }
+  an = block_sum(an, red);
+  off = block_sum(off, red);
+  rr = block_sum(rr, red);
+  const double delta = 2.0 * (sqrt(off) + sqrt(an) * sqrt(rr));
   double emax = 0.0;
-  for (int e = tid; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e % m;
-    const double r = R[e];
-    double E;
-    if (i != j && fabs(sl[i] - sl[j]) > delta) E = (Sp[e] + sl[j] * r) / (sl[j] - sl[i]);
-    else E = 0.5 * r;
-    R[e] = E;
-    emax = fmax(emax, fabs(E));
+  for (int i = blockIdx.x; i < m; i += gridDim.x) {
+    const double li = lam[i];
+    double* Ri = R + (size_t)i * m;
+    const double* Si = Sp + (size_t)i * m;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double r = Ri[j];
+      const double lj = lam[j];
+      double E;
+      if (j != i && fabs(li - lj) > delta) E = (Si[j] + lj * r) / (lj - li);
+      else E = 0.5 * r;
+      Ri[j] = E;
+      emax = fmax(emax, fabs(E));
+    }
   }
   emax = block_max(emax, red);
-  for (int i = tid; i < m; i += blockDim.x) lam[i] = sl[i];
-  // stop once the correction is at the FP64 rounding level, or once it no
-  // longer shrinks quadratically (near-degenerate pairs leave rounding noise of
-  // order u ||A|| / gap that no further step removes)
-  if (tid == 0) {
+  if (threadIdx.x == 0) emax_part[blockIdx.x] = emax;
+}
+
+// Stop once the correction is at the FP64 rounding level, or once it no
+// longer shrinks quadratically (near-degenerate pairs leave rounding noise of
+// order u ||A|| / gap that no further step removes).
+__global__ void oa_finish_kernel(const double* __restrict__ emax_part, int nparts, int* __restrict__ done,
+                                 double* __restrict__ prev_emax) {
+  if (*done) return;
+  __shared__ double red[32];
+  double emax = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) emax = fmax(emax, emax_part[b]);
+  emax = block_max(emax, red);
+  if (threadIdx.x == 0) {
     const double pe = *prev_emax;
     if (emax <= 4e-16 || (emax < 1e-8 && emax > 0.01 * pe)) *done = 1;
     *prev_emax = emax;

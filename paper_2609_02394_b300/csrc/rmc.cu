@@ -867,15 +867,16 @@ rmc_status jacobi(rmc_ctx* ctx, const TI* S, int m, TO* w, TO* V) {
 // the FP64 rounding level a device flag makes the remaining launches return
 // at once).
 constexpr int kOASteps = 8;
+constexpr int kOAParts = 148;  // CTAs of an Ogita-Aishima step (rows dealt to them)
 
 // The m x m products of the refinement: in the mixed paths in double-float on
 // the FP32 pipe (like their block products), in the FP64 path native FP64.
 template <bool TA, bool TB>
 rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, double* C, double beta,
-                         const double* Src, const int* skip) {
+                         const double* Src, const int* skip, double alpha = 1.0) {
   GemmShape s{m, m, m, m, m, 0, 0, 1};
   s.skip = skip;
-  EpiAxpby<double> epi{C, Src, m, m, 0, 0, 1.0, beta};
+  EpiAxpby<double> epi{C, Src, m, m, 0, 0, alpha, beta};
   if (fp64_by_df(ctx)) launch_gemm<double, 16, 16, 8, 1, 1, TA, TB, EpiAxpby<double>, true>(A, B, s, 1, epi, ctx->stream);
   else gemm_small<double, TA, TB>(A, B, s, 1, epi, ctx->stream);
   CKL();
@@ -888,9 +889,11 @@ rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, 
 // size (no shared-memory bound).
 rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w, double* V,
                   bool from_identity = false) {
-  double *V0, *V1, *R, *AV, *Sp, *lam, *pe;
+  double *V0, *V1, *R, *AV, *Sp, *lam, *pe, *part;
   int* done;
+  const int nparts = std::min(m, kOAParts);
   TRY(ws.get(&pe, 1));
+  TRY(ws.get(&part, (size_t)4 * nparts));
   TRY(ws.get(&V0, (size_t)m * m));
   TRY(ws.get(&V1, (size_t)m * m));
   TRY(ws.get(&R, (size_t)m * m));
@@ -913,7 +916,11 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
     CKL();
     TRY((small_mm_skip<false, false>(ctx, S, V0, m, AV, 0.0, nullptr, done)));
     TRY((small_mm_skip<true, false>(ctx, V0, AV, m, Sp, 0.0, nullptr, done)));
-    oa_correction_kernel<<<1, 512, sizeof(double) * m, ctx->stream>>>(R, Sp, S, m, lam, done, pe);
+    oa_sums_kernel<<<nparts, 256, 0, ctx->stream>>>(R, Sp, S, m, lam, part, done);
+    CKL();
+    oa_update_kernel<<<nparts, 256, 0, ctx->stream>>>(R, Sp, lam, m, part, nparts, part + 3 * nparts, done);
+    CKL();
+    oa_finish_kernel<<<1, 256, 0, ctx->stream>>>(part + 3 * nparts, nparts, done, pe);
     CKL();
     TRY((small_mm_skip<false, false>(ctx, V0, R, m, V1, 1.0, V0, done)));
     copy_unless_kernel<<<grid1d((long)m * m), 256, 0, ctx->stream>>>(V1, V0, m * m, done);
@@ -1725,20 +1732,20 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
     shifted_identity_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(nullptr, b, 1.0, 0.0, Wm);  // W0 = I
     CKL();
     for (int it = 0; it < kInvSqrtSteps; ++it) {
-      TRY((small_mm<double, false, false>(ctx, Wm, Gt, b, S2, -0.5, 0.0, nullptr)));  // -W Y / 2
+      TRY((small_mm_skip<false, false>(ctx, Wm, Gt, b, S2, 0.0, nullptr, nullptr, -0.5)));  // -W Y / 2
       shifted_identity_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(S2, b, 1.5, 1.0, S2);  // T = 3/2 I - W Y / 2
       CKL();
-      TRY((small_mm<double, false, false>(ctx, Gt, S2, b, Tm, 1.0, 0.0, nullptr)));  // Y T
-      TRY((small_mm<double, false, false>(ctx, S2, Wm, b, X1, 1.0, 0.0, nullptr)));  // T W
+      TRY((small_mm_skip<false, false>(ctx, Gt, S2, b, Tm, 0.0, nullptr, nullptr, 1.0)));  // Y T
+      TRY((small_mm_skip<false, false>(ctx, S2, Wm, b, X1, 0.0, nullptr, nullptr, 1.0)));  // T W
       std::swap(Gt, Tm);
       std::swap(Wm, X1);
     }
     scale_inv_sqrt_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(Wm, b, cdev);
     CKL();
-    TRY((small_mm<double, false, false>(ctx, Wm, Gm, b, Tm, 1.0, 0.0, nullptr)));
-    TRY((small_mm<double, false, false>(ctx, Tm, Wm, b, Gt, 1.0, 0.0, nullptr)));
+    TRY((small_mm_skip<false, false>(ctx, Wm, Gm, b, Tm, 0.0, nullptr, nullptr, 1.0)));
+    TRY((small_mm_skip<false, false>(ctx, Tm, Wm, b, Gt, 0.0, nullptr, nullptr, 1.0)));
     TRY(syev64(ctx, ws, Gt, b, w, Zt, true));
-    TRY((small_mm<double, false, false>(ctx, Wm, Zt, b, Zs, 1.0, 0.0, nullptr)));
+    TRY((small_mm_skip<false, false>(ctx, Wm, Zt, b, Zs, 0.0, nullptr, nullptr, 1.0)));
     // new iterate: C Z + E Z and HC Z + HE Z (FP64-accurate combinations of the
     // O(1) parts, FP32 of the small ones); E, HE are reused for E Z, HE Z
     TRY(combine<double>(ctx, Zs, true, b, b, C, n, X, 1.0, 0.0, nullptr));
