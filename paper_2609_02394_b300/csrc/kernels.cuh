@@ -847,6 +847,138 @@ __global__ void __launch_bounds__(1024) jacobi_cleanup_kernel(const double* __re
   for (int i = tid; i < m; i += nt) lam[i] = S[i * m + i];
 }
 
+// The same clean-up for matrices too large for shared memory (m up to 1024;
+// 512 threads, where 1024 made it spill):
+// S is a global m x m scratch (this CTA's own), and each row keeps its largest
+// off-diagonal |S_ij| and its column in shared memory, so a rotation costs
+// O(m) work instead of an O(m^2) search: after rotating (p, q) the rows p and
+// q, and every row whose largest entry sat in column p or q, are scanned again;
+// every other row only compares its two changed entries with its maximum.
+__global__ void __launch_bounds__(512) jacobi_cleanup_global_kernel(const double* __restrict__ Sin, int m,
+                                                                     double* __restrict__ S,
+                                                                     double* __restrict__ V,
+                                                                     double* __restrict__ lam, double tol) {
+  __shared__ double rmax[1024];
+  __shared__ int rarg[1024];
+  __shared__ bool rescan[1024];
+  __shared__ double red[32];
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_p, s_q, s_n;
+  __shared__ double s_c, s_s;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  double fro = 0.0;
+  for (int i = wid; i < m; i += nw)
+    for (int j = lane; j < m; j += 32) {
+      const double v = 0.5 * (Sin[i * m + j] + Sin[j * m + i]);
+      S[i * m + j] = v;
+      fro += v * v;
+    }
+  fro = sqrt(block_sum(fro, red));  // (its barriers also publish S to the CTA)
+  const double thresh = tol * fro;
+  // largest off-diagonal entry of row i (ties: the lowest column), by one warp
+  auto scan_row = [&](int i) {
+    double best = -1.0;
+    int arg = i == 0 ? 1 : 0;
+    for (int j = lane; j < m; j += 32) {
+      const double a = j == i ? -1.0 : fabs(S[i * m + j]);
+      if (a > best) { best = a; arg = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+      if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    }
+    if (lane == 0) { rmax[i] = best; rarg[i] = arg; }
+  };
+  for (int i = wid; i < m; i += nw) scan_row(i);
+  __syncthreads();
+  for (int rot = 0; rot < 4 * m; ++rot) {
+    // the row with the largest entry (ties: the lowest row)
+    double best = -1.0;
+    int bi = 0;
+    for (int i = tid; i < m; i += nt)
+      if (rmax[i] > best) { best = rmax[i]; bi = i; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { sv[wid] = best; si[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      int w = 0;
+      for (int j = 1; j < nw; ++j)
+        if (sv[j] > sv[w] || (sv[j] == sv[w] && si[j] < si[w])) w = j;
+      const int a = si[w], b = rarg[si[w]];
+      s_p = a < b ? a : b;
+      s_q = a < b ? b : a;
+      sv[0] = sv[w];
+      if (sv[w] > thresh) {
+        const int p = s_p, q = s_q;
+        const double apq = S[p * m + q], app = S[p * m + p], aqq = S[q * m + q];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        s_c = 1.0 / sqrt(1.0 + t * t);
+        s_s = t * s_c;
+      }
+    }
+    __syncthreads();
+    if (!(sv[0] > thresh)) break;
+    const int p = s_p, q = s_q;
+    const double c = s_c, s = s_s;
+    for (int j = tid; j < m; j += nt) {
+      const double ap = S[p * m + j], aq = S[q * m + j];
+      S[p * m + j] = c * ap - s * aq;
+      S[q * m + j] = s * ap + c * aq;
+    }
+    __syncthreads();
+    for (int j = tid; j < m; j += nt) {
+      const double ap = S[j * m + p], aq = S[j * m + q];
+      S[j * m + p] = c * ap - s * aq;
+      S[j * m + q] = s * ap + c * aq;
+      const double vp = V[j * m + p], vq = V[j * m + q];
+      V[j * m + p] = c * vp - s * vq;
+      V[j * m + q] = s * vp + c * vq;
+    }
+    __syncthreads();
+    if (tid == 0) { S[p * m + q] = 0.0; S[q * m + p] = 0.0; }
+    __syncthreads();
+    // row maxima: cheap updates first, then the rows to scan again
+    for (int i = tid; i < m; i += nt) {
+      rescan[i] = i == p || i == q || rarg[i] == p || rarg[i] == q;
+      if (rescan[i]) continue;
+      const double ap = fabs(S[i * m + p]), aq = fabs(S[i * m + q]);
+      const int lo = p < q ? p : q, hi = p < q ? q : p;
+      const double alo = lo == p ? ap : aq, ahi = lo == p ? aq : ap;
+      if (alo > rmax[i] || (alo == rmax[i] && lo < rarg[i])) { rmax[i] = alo; rarg[i] = lo; }
+      if (ahi > rmax[i] || (ahi == rmax[i] && hi < rarg[i])) { rmax[i] = ahi; rarg[i] = hi; }
+    }
+    __syncthreads();
+    if (tid == 0) {  // the rows to scan again (more than 32: all rows, rare)
+      int cnt = 0;
+      bool all = false;
+      for (int i = 0; i < m; ++i)
+        if (rescan[i]) {
+          if (cnt < 32) si[cnt++] = i;
+          else all = true;
+        }
+      s_n = all ? -1 : cnt;
+    }
+    __syncthreads();
+    const int nscan = s_n;
+    if (nscan >= 0) {
+      for (int r = wid; r < nscan; r += nw) scan_row(si[r]);
+    } else {
+      for (int i = wid; i < m; i += nw) scan_row(i);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += nt) lam[i] = S[i * m + i];
+}
+
 // V = I (m x m)
 __global__ void identity_fill_kernel(double* __restrict__ V, int m) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)

@@ -889,6 +889,7 @@ rmc_status small_mm_skip(rmc_ctx* ctx, const double* A, const double* B, int m, 
 // size (no shared-memory bound).
 rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w, double* V,
                   bool from_identity = false) {
+  if (m < 1 || m > 1024) return fail(ctx, RMC_ERR_INVAL, "small eigensolver: m=%d outside [1, 1024]", m);
   double *V0, *V1, *R, *AV, *Sp, *lam, *pe, *part;
   int* done;
   const int nparts = std::min(m, kOAParts);
@@ -939,6 +940,13 @@ rmc_status syev64(rmc_ctx* ctx, Workspace& ws, const double* S, int m, double* w
     CK(cudaFuncSetAttribute(jacobi_cleanup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(double) * kMaxSmallDim * kMaxSmallDim)));
     jacobi_cleanup_kernel<<<1, 1024, sizeof(double) * m * m, ctx->stream>>>(Sp, m, V1, lam, 1e-14);
+    CKL();
+  } else {
+    // the same for a matrix too large for shared memory (V0 is free here and
+    // holds the working copy of Sp)
+    TRY((small_mm_skip<false, false>(ctx, S, V1, m, AV, 0.0, nullptr, nullptr)));
+    TRY((small_mm_skip<true, false>(ctx, V1, AV, m, Sp, 0.0, nullptr, nullptr)));
+    jacobi_cleanup_global_kernel<<<1, 512, 0, ctx->stream>>>(Sp, m, V0, V1, lam, 1e-14);
     CKL();
   }
   sort_pairs_kernel<<<1, 256, 0, ctx->stream>>>(lam, V1, m, w, V);
