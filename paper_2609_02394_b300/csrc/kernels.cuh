@@ -1128,26 +1128,53 @@ __global__ void axpby_kernel(const T* __restrict__ P, const T* __restrict__ Q, l
 }
 
 // Refinement in defect form (the mixed paths' FP64 refinement of wide
-// blocks).  Rf = HC - C diag(w): the Ritz residuals, formed in FP64 and kept
-// in FP32 (they are small; FP32 keeps them to ~6e-8 of their own size).
+// blocks).  The per-column kernels below take a grid of (chunks of n, rows):
+// blockIdx.y is the vector, so no index is divided per element.
+inline dim3 rows_grid(long n, int rows) {
+  const long chunks = (n + 1023) / 1024;
+  return dim3((unsigned)std::max(1L, std::min(chunks, 64L)), (unsigned)std::max(1, rows));
+}
+
+// dst[j] = src[idx[j]] for whole vectors of length n (vector-major blocks)
+template <typename T>
+__global__ void gather_rows_kernel(const T* __restrict__ src, const int* __restrict__ idx, long n, T* __restrict__ dst) {
+  const T* sr = src + (long)idx[blockIdx.y] * n;
+  T* dr = dst + (long)blockIdx.y * n;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x) dr[r] = sr[r];
+}
+
+// dst[idx[j]] = src[j] for whole vectors of length n
+template <typename T>
+__global__ void scatter_rows_kernel(const T* __restrict__ src, const int* __restrict__ idx, long n, T* __restrict__ dst) {
+  const T* sr = src + (long)blockIdx.y * n;
+  T* dr = dst + (long)idx[blockIdx.y] * n;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x) dr[r] = sr[r];
+}
+
+// dst[idx[j]] = src[j], j < count
+__global__ void scatter_values_kernel(const double* __restrict__ src, const int* __restrict__ idx, int count,
+                                      double* __restrict__ dst) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < count) dst[idx[j]] = src[j];
+}
+
+// Rf = HC - C diag(w): the Ritz residuals, formed in FP64 and kept in FP32
+// (they are small; FP32 keeps them to ~6e-8 of their own size).
 __global__ void ritz_residual_kernel(const double* __restrict__ C, const double* __restrict__ HC,
-                                     const double* __restrict__ w, long n, long tot, float* __restrict__ Rf) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
-    Rf[e] = (float)(HC[e] - w[e / n] * C[e]);
+                                     const double* __restrict__ w, long n, float* __restrict__ Rf) {
+  const long o = (long)blockIdx.y * n;
+  const double wi = w[blockIdx.y];
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    Rf[o + r] = (float)(HC[o + r] - wi * C[o + r]);
 }
 
 // D[i][r] += s[i] * Rf[i][r]: the source term of the defect recurrence.
 __global__ void add_scaled_columns_kernel(float* __restrict__ D, const float* __restrict__ Rf,
-                                          const float* __restrict__ s, long n, long tot) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
-    D[e] += s[e / n] * Rf[e];
-}
-
-// X[i][r] = y[i] C[i][r] + D[i][r]: the filtered block, p(H) C = C p(Theta) + D.
-__global__ void defect_combine_kernel(const double* __restrict__ C, const double* __restrict__ y,
-                                      const float* __restrict__ D, long n, long tot, double* __restrict__ X) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
-    X[e] = y[e / n] * C[e] + (double)D[e];
+                                          const float* __restrict__ s, long n) {
+  const long o = (long)blockIdx.y * n;
+  const float si = s[blockIdx.y];
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    D[o + r] += si * Rf[o + r];
 }
 
 // Y += F (FP32 addend into FP64).
@@ -1183,11 +1210,14 @@ __global__ void defect_gram_kernel(const double* __restrict__ SCE, const float* 
 }
 
 // E[i][r] = (float)(Dperp[i][r] / y[i]): each filtered column's correction
-// outside span C, relative to its own amplification.
-__global__ void scale_columns_inv_kernel(const float* __restrict__ D, const double* __restrict__ y, long n, long tot,
+// outside span C, relative to its own amplification (one FP64 reciprocal a
+// vector; the per-entry product in FP64).
+__global__ void scale_columns_inv_kernel(const float* __restrict__ D, const double* __restrict__ y, long n,
                                          float* __restrict__ E) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
-    E[e] = (float)((double)D[e] / y[e / n]);
+  const long o = (long)blockIdx.y * n;
+  const double inv = 1.0 / y[blockIdx.y];
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    E[o + r] = (float)((double)D[o + r] * inv);
 }
 
 // out = alpha I + beta A (m x m).

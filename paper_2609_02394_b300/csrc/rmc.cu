@@ -1578,14 +1578,17 @@ rmc_status prepare_kron(rmc_ctx* ctx, Workspace& ws, const MergeInput& in, KronO
 // FP64-accurate Gram and combination products; the merge's only FP64-accurate
 // Kronecker product is the first one, of the working-precision block.
 //
+// After the first pass a pass works on the active columns only: the kept
+// vectors that still fail the residual test and the guard columns.  Their
+// defects are projected against the whole basis, so the active block Q_S is
+// orthogonal to the fixed columns, whose coupling to it through H is second
+// order (E_S^T R_fixed); the Rayleigh-Ritz step runs on span Q_S alone, and
+// every product of the pass is sized by the active count (on the 65536-row
+// merges about a third of the block on the second pass and an eighth after).
+//
 // The passes stop when the kept vectors pass the residual test, after
 // max_passes, or after two passes in a row that did not halve the worst
-// residual.  On the 128-site k = 256 chain 12 of 14 merges of dimension 65536
-// pass the 1e-8 test in 3-5 passes; two stop at 5e-8 and 1.6e-7 on 2-4
-// vectors whose residuals barely move under further passes of either this
-// form or a fully FP64-accurate one (double-FP32 Gram and combination
-// products), and the chain's energies still agree with the plain FP64 path to
-// 6e-11.
+// residual.
 //
 // The filter covers the whole block at once (no chunks); its amplification
 // ratio is capped (kDefectRho) so that the guard columns' corrections stay
@@ -1634,23 +1637,49 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
   TRY(syev64(ctx, ws, G, b, w, Z, true));
   TRY(combine<double>(ctx, Z, true, b, b, X, n, C, 1.0, 0.0, nullptr));
   TRY(combine<double>(ctx, Z, true, b, b, HX, n, HC, 1.0, 0.0, nullptr));
-  std::vector<double> th(b), y0(b), y1(b), y2(b), r(b);
+  // A pass refines only the active columns: the kept vectors that still fail
+  // the residual test and the guard columns (the rest stay as they are).
+  // Their corrections are projected against the whole basis C, so Q_S =
+  // C_S + E_S is orthogonal to the fixed columns, which are Ritz vectors with
+  // residuals below tol: the coupling Q_S^T H C_fixed = E_S^T R_fixed is
+  // second order, and the Rayleigh-Ritz step is taken on span Q_S alone.
+  // Columns keep their physical slots; the order by Ritz value is taken on
+  // the host each pass and made physical at the end.
+  std::vector<double> th(b), y0(b), y1(b), y2(b), r(b), tha(b);
   std::vector<float> sc((size_t)kDefectMaxDeg * b);
+  std::vector<int> order(b), act;
+  int* act_dev;
+  double *Cs, *HCs, *wa;
+  TRY(ws.get(&act_dev, (size_t)b));
+  TRY(ws.get(&Cs, (size_t)tot));
+  TRY(ws.get(&HCs, (size_t)tot));
+  TRY(ws.get(&wa, (size_t)b));
+  float* Cfs;
+  TRY(ws.get(&Cfs, (size_t)tot));
+  auto sorted_order = [&]() {
+    for (int i = 0; i < b; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return th[x] < th[y]; });
+  };
+  auto failing = [&](int i) { return !(r[i] <= tol * std::max(1.0, std::fabs(th[i]))); };
   double prev_worst = 1e300;
   int stalled = 0;
   for (int pass = 0;; ++pass) {
-    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-    residual_kernel<double><<<b, 256, 0, ctx->stream>>>(C, HC, w, n, k_acc, tol, rn, ctx->d_status);
+    residual_kernel<double><<<b, 256, 0, ctx->stream>>>(C, HC, w, n, 0, tol, rn, ctx->d_status);
     CKL();
-    int fails = 0;
-    TRY(read_status(ctx, &fails, 1));
     TRY(to_host<double>(ctx, w, th.data(), b));
     TRY(to_host<double>(ctx, rn, r.data(), b));
-    int wi = 0;
-    const double worst = worst_relative(r, th, k_acc, &wi);
+    sorted_order();
+    int fails = 0, wi = order[0];
+    double worst = 0.0;
+    for (int pos = 0; pos < k_acc; ++pos) {
+      const int i = order[pos];
+      const double v = r[i] / std::max(1.0, std::fabs(th[i]));
+      if (failing(i)) ++fails;
+      if (v > worst) { worst = v; wi = i; }
+    }
     if (ctx->trace)
-      fprintf(stderr, "[rmc refine defect] n=%ld b=%d pass=%d fails=%d worst i=%d res=%.3e theta=%.12g thb=%.12g\n", n,
-              b, pass, fails, wi, worst, th[wi], th[b - 1]);
+      fprintf(stderr, "[rmc refine defect] n=%ld b=%d pass=%d fails=%d worst res=%.3e theta=%.12g thb=%.12g\n", n, b,
+              pass, fails, worst, th[wi], th[order[b - 1]]);
     if (fails == 0 || pass >= max_passes) break;
     // two passes in a row without halving the worst residual: the remaining
     // vectors converge too slowly to be worth more passes (the energies they
@@ -1658,24 +1687,32 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
     stalled = (pass > 0 && worst > 0.5 * prev_worst) ? stalled + 1 : 0;
     if (stalled >= 2) break;
     prev_worst = worst;
-    const double a = th[b - 1], e = (ub - a) / 2, c = (ub + a) / 2;
+    act.clear();
+    for (int pos = 0; pos < b; ++pos)
+      if (pos >= k_acc || failing(order[pos])) act.push_back(order[pos]);
+    std::sort(act.begin(), act.end());
+    const int na = (int)act.size();
+    const long tota = (long)na * n;
+    const double a = th[order[b - 1]], e = (ub - a) / 2, c = (ub + a) / 2;
     if (!(e > 0)) break;
-    const double x0 = std::fabs((th[0] - c) / e);
+    const double tlo = th[order[0]];
+    const double x0 = std::fabs((tlo - c) / e);
     int deg = (int)std::floor(std::acosh(kDefectRho) / std::acosh(std::max(x0, 1.0 + 1e-12)));
     deg = std::max(2, std::min(kDefectMaxDeg, deg));
-    // scalar recurrence at the Ritz values and the per-column source scales
-    double sigma = e / (th[0] - c);
+    // scalar recurrence at the active Ritz values and their source scales
+    double sigma = e / (tlo - c);
     const double tau = 2.0 / sigma;
-    for (int i = 0; i < b; ++i) {
-      y0[i] = 1.0;
-      y1[i] = sigma / e * (th[i] - c);
+    for (int j = 0; j < na; ++j) {
+      tha[j] = th[act[j]];
+      y0[j] = 1.0;
+      y1[j] = sigma / e * (tha[j] - c);
     }
     std::vector<double> s_of(deg + 1);
     for (int d = 2; d <= deg; ++d) {
       const double s1 = 1.0 / (tau - sigma);
-      for (int i = 0; i < b; ++i) {
-        sc[(size_t)(d - 2) * b + i] = (float)(2 * s1 / e * y1[i]);
-        y2[i] = 2 * s1 / e * (th[i] - c) * y1[i] - sigma * s1 * y0[i];
+      for (int j = 0; j < na; ++j) {
+        sc[(size_t)(d - 2) * na + j] = (float)(2 * s1 / e * y1[j]);
+        y2[j] = 2 * s1 / e * (tha[j] - c) * y1[j] - sigma * s1 * y0[j];
       }
       std::swap(y0, y1);
       std::swap(y1, y2);
@@ -1683,23 +1720,31 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
       sigma = s1;
     }
     // (pageable sources: the copies are staged before the calls return)
-    CK(cudaMemcpyAsync(sdev, sc.data(), sizeof(float) * (size_t)(deg - 1) * b, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ydev, y1.data(), sizeof(double) * b, cudaMemcpyHostToDevice, ctx->stream));
-    // FP32 copies of the iterate, the residuals, and the defect recurrence
+    CK(cudaMemcpyAsync(sdev, sc.data(), sizeof(float) * (size_t)(deg - 1) * na, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ydev, y1.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(wa, tha.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(act_dev, act.data(), sizeof(int) * na, cudaMemcpyHostToDevice, ctx->stream));
+    // the active columns, FP32 copies, residuals and the defect recurrence
+    gather_rows_kernel<double><<<rows_grid(n, na), 256, 0, ctx->stream>>>(C, act_dev, n, Cs);
+    CKL();
+    gather_rows_kernel<double><<<rows_grid(n, na), 256, 0, ctx->stream>>>(HC, act_dev, n, HCs);
+    CKL();
     convert_kernel<float, double><<<grid1d(tot), 256, 0, ctx->stream>>>(C, Cf, tot);
     CKL();
-    ritz_residual_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(C, HC, w, n, tot, Rf);
+    convert_kernel<float, double><<<grid1d(tota), 256, 0, ctx->stream>>>(Cs, Cfs, tota);
     CKL();
-    CK(cudaMemsetAsync(D0, 0, sizeof(float) * tot, ctx->stream));
-    sigma = e / (th[0] - c);
-    axpby_kernel<float><<<grid1d(tot), 256, 0, ctx->stream>>>(Rf, Rf, tot, (float)(sigma / e), 0.0f, D1);
+    ritz_residual_kernel<<<rows_grid(n, na), 256, 0, ctx->stream>>>(Cs, HCs, wa, n, Rf);
+    CKL();
+    CK(cudaMemsetAsync(D0, 0, sizeof(float) * tota, ctx->stream));
+    sigma = e / (tlo - c);
+    axpby_kernel<float><<<grid1d(tota), 256, 0, ctx->stream>>>(Rf, Rf, tota, (float)(sigma / e), 0.0f, D1);
     CKL();
     float *Dp = D0, *Dc = D1, *Dn = D2;
     for (int d = 2; d <= deg; ++d) {
       const double s1 = s_of[d];
-      TRY(kron_work<float>(ctx, Hf, Dc, b, Dn, (float)(2 * s1 / e), (float)(-2 * s1 * c / e), (float)(-sigma * s1), Dp,
+      TRY(kron_work<float>(ctx, Hf, Dc, na, Dn, (float)(2 * s1 / e), (float)(-2 * s1 * c / e), (float)(-sigma * s1), Dp,
                            Tf));
-      add_scaled_columns_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(Dn, Rf, sdev + (size_t)(d - 2) * b, n, tot);
+      add_scaled_columns_kernel<<<rows_grid(n, na), 256, 0, ctx->stream>>>(Dn, Rf, sdev + (size_t)(d - 2) * na, n);
       CKL();
       float* t = Dp;
       Dp = Dc;
@@ -1707,67 +1752,85 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
       Dn = t;
       sigma = s1;
     }
-    // D = C G1 + D_perp (in place), E = D_perp diag(1/y)
+    // D = C G1 + D_perp (in place, against the whole basis), E = D_perp diag(1/y)
     {
       Workspace wl(ctx);
-      TRY(gram<float>(ctx, wl, Cf, b, Dc, b, n, G1, false));
-      TRY(combine<float>(ctx, G1, true, b, b, Cf, n, Dc, -1.0f, 1.0f, Dc));
-      TRY(gram<float>(ctx, wl, Cf, b, Rf, b, n, CR, false));
+      TRY(gram<float>(ctx, wl, Cf, b, Dc, na, n, G1, false));
+      TRY(combine<float>(ctx, G1, true, na, b, Cf, n, Dc, -1.0f, 1.0f, Dc));
+      TRY(gram<float>(ctx, wl, Cfs, na, Rf, na, n, CR, false));
     }
-    scale_columns_inv_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(Dc, ydev, n, tot, E);
+    scale_columns_inv_kernel<<<rows_grid(n, na), 256, 0, ctx->stream>>>(Dc, ydev, n, E);
     CKL();
     // H E on the FP32 pipe, not in 3xTF32: it enters the new H C directly, and
     // the large corrections of the guard columns would carry the tensor-core
     // form's ~5e-7 relative error into the kept vectors through the rotation
-    TRY(kron_apply<float>(ctx, Hf, E, b, HE, 1.0f, 0.0f, 0.0f, nullptr, Tf));
+    TRY(kron_apply<float>(ctx, Hf, E, na, HE, 1.0f, 0.0f, 0.0f, nullptr, Tf));
     {
       Workspace wl(ctx);
-      convert_kernel<double, float><<<grid1d(tot), 256, 0, ctx->stream>>>(E, X, tot);   // E exactly, in FP64
+      convert_kernel<double, float><<<grid1d(tota), 256, 0, ctx->stream>>>(E, X, tota);  // E exactly, in FP64
       CKL();
-      TRY(gram<double>(ctx, wl, C, b, X, b, n, SCE, false));
-      TRY(gram<float>(ctx, wl, E, b, E, b, n, SEE, true));
-      TRY(gram<float>(ctx, wl, Rf, b, E, b, n, RE, false));
-      TRY(gram<float>(ctx, wl, E, b, HE, b, n, EHE, false));
+      TRY(gram<double>(ctx, wl, Cs, na, X, na, n, SCE, false));
+      TRY(gram<float>(ctx, wl, E, na, E, na, n, SEE, true));
+      TRY(gram<float>(ctx, wl, Rf, na, E, na, n, RE, false));
+      TRY(gram<float>(ctx, wl, E, na, HE, na, n, EHE, false));
     }
-    defect_gram_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(SCE, SEE, CR, RE, EHE, w, b, S, Gm);
+    const size_t aa = (size_t)na * na;
+    defect_gram_kernel<<<grid1d((long)aa), 256, 0, ctx->stream>>>(SCE, SEE, CR, RE, EHE, wa, na, S, Gm);
     CKL();
     // W = (I + S)^{-1/2} by the coupled Newton-Schulz iteration on (I + S)/c
     // (Y -> its square root, W -> its inverse square root; the corrections of
     // unconverged guard columns make S far from small, so the spectrum is
     // first scaled into [1/c, 1]); Gt = W Gm W; its eigenpairs; Z = W Zt
-    ns_start_kernel<<<1, 1024, 0, ctx->stream>>>(S, SEE, b, Gt, cdev);   // Y0 = (I + S) / c
+    ns_start_kernel<<<1, 1024, 0, ctx->stream>>>(S, SEE, na, Gt, cdev);   // Y0 = (I + S) / c
     CKL();
-    shifted_identity_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(nullptr, b, 1.0, 0.0, Wm);  // W0 = I
+    shifted_identity_kernel<<<grid1d((long)aa), 256, 0, ctx->stream>>>(nullptr, na, 1.0, 0.0, Wm);  // W0 = I
     CKL();
     for (int it = 0; it < kInvSqrtSteps; ++it) {
-      TRY((small_mm_skip<false, false>(ctx, Wm, Gt, b, S2, 0.0, nullptr, nullptr, -0.5)));  // -W Y / 2
-      shifted_identity_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(S2, b, 1.5, 1.0, S2);  // T = 3/2 I - W Y / 2
+      TRY((small_mm_skip<false, false>(ctx, Wm, Gt, na, S2, 0.0, nullptr, nullptr, -0.5)));  // -W Y / 2
+      shifted_identity_kernel<<<grid1d((long)aa), 256, 0, ctx->stream>>>(S2, na, 1.5, 1.0, S2);  // T = 3/2 I - W Y / 2
       CKL();
-      TRY((small_mm_skip<false, false>(ctx, Gt, S2, b, Tm, 0.0, nullptr, nullptr, 1.0)));  // Y T
-      TRY((small_mm_skip<false, false>(ctx, S2, Wm, b, X1, 0.0, nullptr, nullptr, 1.0)));  // T W
+      TRY((small_mm_skip<false, false>(ctx, Gt, S2, na, Tm, 0.0, nullptr, nullptr, 1.0)));  // Y T
+      TRY((small_mm_skip<false, false>(ctx, S2, Wm, na, X1, 0.0, nullptr, nullptr, 1.0)));  // T W
       std::swap(Gt, Tm);
       std::swap(Wm, X1);
     }
-    scale_inv_sqrt_kernel<<<grid1d((long)bb), 256, 0, ctx->stream>>>(Wm, b, cdev);
+    scale_inv_sqrt_kernel<<<grid1d((long)aa), 256, 0, ctx->stream>>>(Wm, na, cdev);
     CKL();
-    TRY((small_mm_skip<false, false>(ctx, Wm, Gm, b, Tm, 0.0, nullptr, nullptr, 1.0)));
-    TRY((small_mm_skip<false, false>(ctx, Tm, Wm, b, Gt, 0.0, nullptr, nullptr, 1.0)));
-    TRY(syev64(ctx, ws, Gt, b, w, Zt, true));
-    TRY((small_mm_skip<false, false>(ctx, Wm, Zt, b, Zs, 0.0, nullptr, nullptr, 1.0)));
-    // new iterate: C Z + E Z and HC Z + HE Z (FP64-accurate combinations of the
-    // O(1) parts, FP32 of the small ones); E, HE are reused for E Z, HE Z
-    TRY(combine<double>(ctx, Zs, true, b, b, C, n, X, 1.0, 0.0, nullptr));
-    TRY(combine<double>(ctx, Zs, true, b, b, HC, n, HX, 1.0, 0.0, nullptr));
-    convert_kernel<float, double><<<grid1d((long)bb), 256, 0, ctx->stream>>>(Zs, Af, (long)bb);
+    TRY((small_mm_skip<false, false>(ctx, Wm, Gm, na, Tm, 0.0, nullptr, nullptr, 1.0)));
+    TRY((small_mm_skip<false, false>(ctx, Tm, Wm, na, Gt, 0.0, nullptr, nullptr, 1.0)));
+    TRY(syev64(ctx, ws, Gt, na, wa, Zt, true));
+    TRY((small_mm_skip<false, false>(ctx, Wm, Zt, na, Zs, 0.0, nullptr, nullptr, 1.0)));
+    // new active columns: C_S Z + E Z and HC_S Z + HE Z (FP64-accurate
+    // combinations of the O(1) parts, FP32 of the small ones), back to their slots
+    TRY(combine<double>(ctx, Zs, true, na, na, Cs, n, X, 1.0, 0.0, nullptr));
+    TRY(combine<double>(ctx, Zs, true, na, na, HCs, n, HX, 1.0, 0.0, nullptr));
+    convert_kernel<float, double><<<grid1d((long)aa), 256, 0, ctx->stream>>>(Zs, Af, (long)aa);
     CKL();
-    TRY(combine<float>(ctx, Af, true, b, b, E, n, D0, 1.0f, 0.0f, nullptr));
-    TRY(combine<float>(ctx, Af, true, b, b, HE, n, D1, 1.0f, 0.0f, nullptr));
-    add_f32_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(X, D0, tot);
+    TRY(combine<float>(ctx, Af, true, na, na, E, n, D0, 1.0f, 0.0f, nullptr));
+    TRY(combine<float>(ctx, Af, true, na, na, HE, n, D1, 1.0f, 0.0f, nullptr));
+    add_f32_kernel<<<grid1d(tota), 256, 0, ctx->stream>>>(X, D0, tota);
     CKL();
-    add_f32_kernel<<<grid1d(tot), 256, 0, ctx->stream>>>(HX, D1, tot);
+    add_f32_kernel<<<grid1d(tota), 256, 0, ctx->stream>>>(HX, D1, tota);
     CKL();
-    std::swap(C, X);
-    std::swap(HC, HX);
+    scatter_rows_kernel<double><<<rows_grid(n, na), 256, 0, ctx->stream>>>(X, act_dev, n, C);
+    CKL();
+    scatter_rows_kernel<double><<<rows_grid(n, na), 256, 0, ctx->stream>>>(HX, act_dev, n, HC);
+    CKL();
+    scatter_values_kernel<<<ceil_div(na, 256), 256, 0, ctx->stream>>>(wa, act_dev, na, w);
+    CKL();
+  }
+  // the Ritz pairs in ascending order
+  TRY(to_host<double>(ctx, w, th.data(), b));
+  sorted_order();
+  bool permuted = false;
+  for (int i = 0; i < b; ++i) permuted |= order[i] != i;
+  if (permuted) {
+    for (int i = 0; i < b; ++i) tha[i] = th[order[i]];
+    CK(cudaMemcpyAsync(act_dev, order.data(), sizeof(int) * b, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(w, tha.data(), sizeof(double) * b, cudaMemcpyHostToDevice, ctx->stream));
+    gather_rows_kernel<double><<<rows_grid(n, b), 256, 0, ctx->stream>>>(C, act_dev, n, X);
+    CKL();
+    CK(cudaMemcpyAsync(C, X, sizeof(double) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   // the basis to FP64 orthonormality (each pass left it within ~1e-11)
   TRY(cholqr64_refine(ctx, ws, C, b, n, X));
