@@ -1055,60 +1055,87 @@ __global__ void __launch_bounds__(cholinv_threads<TC>()) cholinv_kernel(const TI
       return;
     }
   }
+  // L uses an odd row stride, so the column accesses of the factorisation and
+  // of the solves hit distinct shared-memory banks (an even m put a whole
+  // warp's column reads on one bank); dg holds the factor's diagonal, then
+  // its reciprocals.
+  const int ld = m | 1;
+  TC* dg = L + (size_t)m * ld;
   TC dmax = 0;
   for (int i = tid; i < m; i += nt) dmax = fmax(dmax, (TC)G[i * m + i]);
   dmax = block_max(dmax, red);
   const TC sh = (TC)shift * dmax;
   for (int i = warp; i < m; i += nw)
     for (int j = lane; j < m; j += 32)
-      L[i * m + j] = (j <= i) ? (TC)(0.5 * ((double)G[i * m + j] + (double)G[j * m + i])) + (i == j ? sh : TC(0))
-                              : TC(0);
+      L[i * ld + j] = (j <= i) ? (TC)(0.5 * ((double)G[i * m + j] + (double)G[j * m + i])) + (i == j ? sh : TC(0))
+                               : TC(0);
   __syncthreads();
   const TC tiny = dmax * (TC)1e-30 + (TC)(sizeof(TC) == 4 ? 1e-37 : 1e-300);
   for (int j = 0; j < m; ++j) {
-    // every thread reads the pivot and scales its own entries of column j
-    TC d = L[j * m + j];
+    // every thread reads the pivot (no thread writes it during this column)
+    // and scales its own entries of column j
+    TC d = L[j * ld + j];
     bool bad = !(d > tiny);
     if (bad) d = fmax(dmax, tiny) * (TC)1e-12;
     const TC ljj = sqrt(d);
     const TC inv = TC(1) / ljj;
-    __syncthreads();
     if (tid == 0) {
-      L[j * m + j] = ljj;
+      dg[j] = ljj;
       if (bad && status) atomicAdd(status, 1);
     }
-    for (int i = j + 1 + tid; i < m; i += nt) L[i * m + j] *= inv;
+    for (int i = j + 1 + tid; i < m; i += nt) L[i * ld + j] *= inv;
     __syncthreads();
     for (int i = j + 1 + warp; i < m; i += nw) {
-      const TC lij = L[i * m + j];
-      for (int k = j + 1 + lane; k <= i; k += 32) L[i * m + k] -= lij * L[k * m + j];
+      const TC lij = L[i * ld + j];
+      for (int k = j + 1 + lane; k <= i; k += 32) L[i * ld + k] -= lij * L[k * ld + j];
     }
     __syncthreads();
   }
-  // L^{-1}, one warp per column c, no block-wide synchronisation: for i > c,
-  //   Li[i][c] = -(sum_{t=c}^{i-1} L[i][t] Li[t][c]) / L[i][i],  Li[c][c] = 1 / L[c][c],
-  // with Li[t][c] (t > c) kept at L[c*m + t] (the strict upper triangle).
+  for (int i = tid; i < m; i += nt) {
+    L[i * ld + i] = dg[i];
+    dg[i] = TC(1) / dg[i];
+  }
+  __syncthreads();
+  // L^{-1} by columns, one warp per column c: forward substitution of
+  // L y = e_c with y held in registers (lane l owns y_{l + 32 q}); step t
+  // finishes y_t on its owner lane, broadcasts it, and every lane removes it
+  // from its later rows.  Li[i][c] (i > c) goes to L[c*ld + i], the strict
+  // upper triangle, which the factor does not use.
+  constexpr int kQ = (kMaxSmallDim + 31) / 32;
   for (int c = warp; c < m; c += nw) {
-    const TC dcc = TC(1) / L[c * m + c];
-    for (int i = c + 1; i < m; ++i) {
-      TC acc = 0;
-      for (int t = c + lane; t < i; t += 32) acc += L[i * m + t] * ((t == c) ? dcc : L[c * m + t]);
-      acc = warp_sum(acc);
-      if (lane == 0) L[c * m + i] = -acc / L[i * m + i];
-      __syncwarp();
+    TC y[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) y[q] = (lane + 32 * q == c) ? TC(1) : TC(0);
+#pragma unroll
+    for (int q0 = 0; q0 < kQ; ++q0) {  // y_t lives in y[q0] of lane t % 32
+      const int t1 = min(m, 32 * q0 + 32);
+      for (int t = max(c, 32 * q0); t < t1; ++t) {
+        const TC yt = __shfl_sync(0xffffffffu, y[q0], t & 31) * dg[t];
+#pragma unroll
+        for (int q = q0; q < kQ; ++q) {  // rows i > t >= 32 q0 only
+          const int i = lane + 32 * q;
+          if (i == t) y[q] = yt;
+          else if (i > t && i < m) y[q] -= L[i * ld + t] * yt;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = lane + 32 * q;
+      if (i > c && i < m) L[c * ld + i] = y[q];
     }
   }
   __syncthreads();
   for (int i = warp; i < m; i += nw)
     for (int c = lane; c < m; c += 32) {
       TO v = TO(0);
-      if (c == i) v = (TO)(TC(1) / L[i * m + i]);
-      else if (c < i) v = (TO)L[c * m + i];
+      if (c == i) v = (TO)dg[i];
+      else if (c < i) v = (TO)L[c * ld + i];
       Linv[i * m + c] = v;
     }
 }
 
-inline size_t cholinv_smem_bytes(int m, size_t elt) { return (size_t)m * m * elt; }
+inline size_t cholinv_smem_bytes(int m, size_t elt) { return ((size_t)m * (m | 1) + m) * elt; }
 
 // out[i][r] = V[r][i] for i < k: the first k columns of a row-major m x m
 // eigenvector matrix as k vectors of length m.

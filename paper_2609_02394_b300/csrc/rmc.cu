@@ -981,7 +981,8 @@ rmc_status cholqr(rmc_ctx* ctx, Workspace& ws, T* X, int nv, long n, T* tmp, dou
 
 // FP64 Cholesky-QR for a nearly orthonormal block: FP32 Cholesky of the FP64
 // Gram matrix, then two first-order FP64 passes (X <- X - F^T X).
-rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long n, double* tmp) {
+rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long n, double* tmp,
+                           int first_order_passes = 2) {
   ProfScope ps(ctx, 3, 0.0);
   double *G, *Li;
   TRY(ws.get(&G, (size_t)nv * nv));
@@ -1004,9 +1005,10 @@ rmc_status cholqr64_refine(rmc_ctx* ctx, Workspace& ws, double* X, int nv, long 
     }
   }
   // first-order passes square the deviation from orthonormality: two take a
-  // block within 1e-3 of orthonormal (a wide block here comes from the FP32
-  // phase, ~1e-6, or from the refinement, ~1e-11) to rounding level
-  for (int pass = 0; pass < 2; ++pass) {
+  // block within 1e-3 of orthonormal (a wide block from the FP32 phase is
+  // within ~1e-6) to rounding level, one suffices for a block within ~1e-8
+  // (the refinement leaves ~1e-11)
+  for (int pass = 0; pass < first_order_passes; ++pass) {
     TRY(gram<double>(ctx, ws, X, nv, X, nv, n, G, true));
     cholqr_first_order_kernel<<<grid1d((long)nv * nv), 256, 0, ctx->stream>>>(G, nv, Li);
     CKL();
@@ -1833,7 +1835,7 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
     CK(cudaMemcpyAsync(C, X, sizeof(double) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   // the basis to FP64 orthonormality (each pass left it within ~1e-11)
-  TRY(cholqr64_refine(ctx, ws, C, b, n, X));
+  TRY(cholqr64_refine(ctx, ws, C, b, n, X, 1));
   if (C != C_out) CK(cudaMemcpyAsync(C_out, C, sizeof(double) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
   return RMC_OK;
 }
