@@ -1112,7 +1112,8 @@ __global__ void __launch_bounds__(cholinv_threads<TC>()) cholinv_kernel(const TI
       for (int t = max(c, 32 * q0); t < t1; ++t) {
         const TC yt = __shfl_sync(0xffffffffu, y[q0], t & 31) * dg[t];
 #pragma unroll
-        for (int q = q0; q < kQ; ++q) {  // rows i > t >= 32 q0 only
+        for (int q = 0; q < kQ; ++q) {
+          if (q < q0) continue;  // rows i > t >= 32 q0 only
           const int i = lane + 32 * q;
           if (i == t) y[q] = yt;
           else if (i > t && i < m) y[q] -= L[i * ld + t] * yt;
