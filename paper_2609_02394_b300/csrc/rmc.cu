@@ -1605,6 +1605,7 @@ rmc_status prepare_kron(rmc_ctx* ctx, Workspace& ws, const MergeInput& in, KronO
 constexpr double kDefectRho = 1e5;
 constexpr int kDefectMaxDeg = 40;
 constexpr int kInvSqrtSteps = 10;
+constexpr double kDefectBlowup = 100.0;  // a pass this much worse than the last is undone
 
 rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>& H64, const KronOp<float>& Hf, int b,
                               int k_acc, double ub, double tol, int max_passes, double* X, double* HX, double* C,
@@ -1684,6 +1685,24 @@ rmc_status refine_wide_defect(rmc_ctx* ctx, Workspace& ws, const KronOp<double>&
     if (ctx->trace)
       fprintf(stderr, "[rmc refine defect] n=%ld b=%d pass=%d fails=%d worst res=%.3e theta=%.12g thb=%.12g\n", n, b,
               pass, fails, worst, th[wi], th[order[b - 1]]);
+    // a pass that made the worst residual far larger (its Rayleigh-Ritz
+    // basis lost a direction: seen once on a 65280-row merge whose guard
+    // columns' corrections were large) is undone: the previous active
+    // columns, their products and Ritz values go back to their slots
+    // (they are still in Cs, HCs, tha and act_dev), and the refinement ends
+    if (pass > 0 && worst > kDefectBlowup * prev_worst) {
+      const int na = (int)act.size();
+      scatter_rows_kernel<double><<<rows_grid(n, na), 256, 0, ctx->stream>>>(Cs, act_dev, n, C);
+      CKL();
+      scatter_rows_kernel<double><<<rows_grid(n, na), 256, 0, ctx->stream>>>(HCs, act_dev, n, HC);
+      CKL();
+      CK(cudaMemcpyAsync(wa, tha.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+      scatter_values_kernel<<<ceil_div(na, 256), 256, 0, ctx->stream>>>(wa, act_dev, na, w);
+      CKL();
+      CK(cudaStreamSynchronize(ctx->stream));  // tha is pageable host memory
+      if (ctx->trace) fprintf(stderr, "[rmc refine defect] n=%ld pass=%d undone (worst %.3e)\n", n, pass, worst);
+      break;
+    }
     if (fails == 0 || pass >= max_passes) break;
     // two passes in a row without halving the worst residual: the remaining
     // vectors converge too slowly to be worth more passes (the energies they
