@@ -49,7 +49,7 @@
 //
 // Every wait is bounded (kSpin polls).  A role that gives up raises the
 // kernel's error flag and leaves its loop; the others then give up too at
-// their own bounded waits.  Before the tensor memory is released the MMA
+// their own bounded waits (the whole-warp roles decide as a warp).  Before the tensor memory is released the MMA
 // thread waits (bounded) for its last MMAs and the producer for its last
 // loads, so no asynchronous write outlives the CTA.
 #pragma once
@@ -202,6 +202,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     *(volatile int*)&aborted = 1;
   };
   auto stopped = [&]() { return *(volatile int*)&aborted != 0; };
+  // the whole-warp roles (converters, epilogue) take every wait decision as a
+  // warp: their loops hold __syncwarp and warp-collective tcgen05.ld, so the
+  // lanes must leave a loop together
+  auto warp_stopped = [&]() { return __any_sync(0xffffffffu, stopped()) != 0; };
+  auto warp_wait = [&](uint64_t* bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity, kSpin) && !stopped();
+    return __all_sync(0xffffffffu, ok) != 0;
+  };
 
   if (warp == 0) {
     // ---- TMA producer ----
@@ -279,13 +287,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- converters: lo parts of the stage's tiles ----
     const int ct = threadIdx.x - kConvWarp0 * 32;
     int it = 0;
-    for (int t = blockIdx.x; t < tiles && !stopped(); t += gridDim.x) {
+    for (int t = blockIdx.x; t < tiles && !warp_stopped(); t += gridDim.x) {
       int mt, nt, ks, kc0, kcs;
       decode(t, &mt, &nt, &ks, &kc0, &kcs);
       bool ok = true;
       for (int kc = 0; kc < kcs; ++kc, ++it) {
         const int s = it % kStages;
-        if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, kSpin) || stopped()) {
+        if (!warp_wait(&full[s], (uint32_t)(it / kStages) & 1u)) {
           ok = false;
           break;
         }
@@ -308,9 +316,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* stg0 = (float*)(base + (size_t)kStages * stage_bytes + (size_t)(warp - kEpiWarp0) * 2 * kStageBlock);
     int sbuf = 0;
     int tc = 0;
-    for (int t = blockIdx.x; t < tiles && !stopped(); t += gridDim.x, ++tc) {
+    for (int t = blockIdx.x; t < tiles && !warp_stopped(); t += gridDim.x, ++tc) {
       const int ab = tc & 1;
-      if (!mbar_wait(&accf[ab], (uint32_t)(tc >> 1) & 1u, kSpin) || stopped()) {
+      if (!warp_wait(&accf[ab], (uint32_t)(tc >> 1) & 1u)) {
         give_up();
         break;
       }
