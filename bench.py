@@ -573,9 +573,9 @@ def run_ours(args):
                               "256 x 256 x 3 operators, 160 vectors)",
                     "bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
                     "frac": achieved / tf32_peak,
-                    "traffic": 2.99e8,
+                    "traffic": 2.95e8,
                     "traffic_note": ("dram bytes read+written by the two launches of one product on this shape "
-                                     "(ncu --set full, profiles/gemm_tma_tf32x3_kron256_nv160.md); algorithmic "
+                                     "(ncu, profiles/gemm_tma_tf32x3_kron256_nv160.md); algorithmic "
                                      "bytes 3.35e8 (X, Y and the 1.26e8-byte intermediate once each)"),
                     "peak_source": (f"TF32 dense tensor peak = measured BF16 burst {pk['bf16']:.1f} x nominal "
                                     f"TF32/BF16 1.1/2.25 ({pk['source']}); 3xTF32 issues three tensor products per "
