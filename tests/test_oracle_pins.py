@@ -339,3 +339,48 @@ def test_subset_eigensolve_equals_full_spectrum():
     np.testing.assert_allclose(blk_sub.E, blk_full.E, atol=1e-11)
     for key in blk_full.ops:
         np.testing.assert_allclose(blk_sub.ops[key], blk_full.ops[key], atol=1e-9)
+
+
+def test_pair_golden_is_bracketed_by_weyl_and_interlacing():
+    """The stored lowest 257 eigenvalues of the dense 65536-dimensional H_eff of
+    the 24-site pair merge (tests/golden/rfheis_pair_n65536.json, LAPACK dsyevr
+    on the oracle's matrix) against bounds that need neither that matrix nor
+    its eigensolver, from Eq. (7) written entry by entry:
+      * Weyl: lambda_i(D + V) >= lambda_i(D) - ||V||_2, D = diag(E_A[a] + E_B[b]),
+        ||V||_2 <= sum_j |c_j| ||o_A^j||_2 ||o_B^j||_2;
+      * Cauchy interlacing: lambda_i <= mu_i, the eigenvalues of H_eff
+        compressed to the 2048 product states of smallest diagonal (0.01 above
+        the stored lowest value; the same compression with the coupling's sign
+        flipped has its lowest value 1.2 above it, so a sign or operand error
+        in the stored values breaks the bound);
+    plus the order, the stored k_eff = the cut rule on the stored values, and
+    the leaves' ground energies."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rfheis_pair_n65536.json")))
+    chain = I.rf_heisenberg_pair()
+    assert I.Chain.from_json(g["chain"]) == chain
+    A = O.leaf_block(chain, 0, 12, chain.k)
+    B = O.leaf_block(chain, 12, 24, chain.k)
+    assert [len(A.E), len(B.E)] == g["leaf_k"]
+    np.testing.assert_allclose([A.E[0], B.E[0]], g["leaf_E0"], rtol=0, atol=1e-10)
+    theta = np.array(g["theta"])
+    assert np.all(np.diff(theta) >= 0)
+    assert g["k_eff"] == O.cut_rule(theta, g["k_ret"])
+    terms = [(c, A.ops[ka], B.ops[kb]) for c, ka, kb in O.merge_terms(chain, 0, 12, 12, 24)]
+    kA, kB = len(A.E), len(B.E)
+    diag = (A.E[:, None] + B.E[None, :]).ravel()
+    for c, oa, ob in terms:  # the coupling's own diagonal, o_A[a,a] o_B[b,b]
+        diag = diag + c * np.outer(np.diag(oa), np.diag(ob)).ravel()
+    vnorm = sum(abs(c) * np.linalg.norm(oa, 2) * np.linalg.norm(ob, 2) for c, oa, ob in terms)
+    D0 = np.sort((A.E[:, None] + B.E[None, :]).ravel())
+    assert np.all(theta >= D0[: len(theta)] - vnorm - 1e-9)
+    sel = np.argsort(diag, kind="stable")[:2048]
+    a, b = sel // kB, sel % kB
+    Hs = np.diag(A.E[a] + B.E[b])
+    for c, oa, ob in terms:
+        Hs = Hs + c * oa[np.ix_(a, a)] * ob[np.ix_(b, b)]
+    mu = np.linalg.eigvalsh(Hs)
+    assert np.all(theta <= mu[: len(theta)] + 1e-9)
+    # the bracket is informative: the lowest value sits well inside it
+    assert mu[0] - theta[0] < 0.5 * (mu[0] - (D0[0] - vnorm))
